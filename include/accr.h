@@ -1,0 +1,164 @@
+/*
+ * accr.h -- C ABI of the GB300 runtime for the device side of an OpenACC
+ * accelerator region (IPMACC, arXiv 1412.1127).
+ *
+ * A call is one region (Sec. 1.3: the `kernels` directive marks a region for
+ * the accelerator): arrays already copied in (the `copy(a[start:n])` data
+ * clause of Listing 1a, here device pointers the caller owns), the loop
+ * bounds, and for each `reduction(op:var)` clause the operator and the type
+ * of the variable (Stage 3.4: "performing variable reductions"; Stage 3.7:
+ * the reduction merge across thread blocks).  A `loop independent` loop is
+ * work-shared gang -> CTA (grid), worker -> warp, vector -> lane (Sec. 1.2
+ * names the four levels; this mapping is the reading used here).
+ *
+ * Conventions for every entry point
+ *  - Pointers named "device" must point to memory of the current CUDA device;
+ *    pointers named "host" to ordinary host memory.  The library never frees
+ *    caller memory.  Scratch space (block partials, counters, split buffers)
+ *    is owned by the library, cached per device and stream, and lives until
+ *    the process exits.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous on `stream` unless ACCR_SYNC is set or stated otherwise.
+ *  - Return value: ACCR_OK (0) or a negative ACCR_E* code.  The message of the
+ *    last error on the calling thread is returned by accr_last_error().  No
+ *    entry point aborts the process.
+ *  - Element arrays must be aligned to their element size.  Any further
+ *    alignment is handled inside (unaligned heads and ragged tails included).
+ *  - Indices and lengths are 64-bit.
+ */
+#ifndef ACCR_H
+#define ACCR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ACCR_API __attribute__((visibility("default")))
+#else
+#define ACCR_API
+#endif
+
+/* A CUDA stream handle (the same type as cudaStream_t). */
+typedef struct CUstream_st *accr_stream_t;
+
+/* Element and reduction-variable types. */
+typedef enum {
+    ACCR_I32 = 0, /* int32_t */
+    ACCR_I64 = 1, /* int64_t */
+    ACCR_F32 = 2, /* float   */
+    ACCR_F64 = 3  /* double  */
+} accr_type;
+
+/* Reduction operators of the reduction clause.  Identities: + 0, * 1,
+ * max lowest (INT_MIN / -inf), min highest (INT_MAX / +inf), & ~0, | 0, ^ 0,
+ * && 1, || 0.  Integer + and * wrap modulo 2^32 / 2^64.  && and || give 0 or 1
+ * (C semantics).  Bitwise and logical operators are defined on integers only.
+ * Floating-point max/min order +0 above -0; NaN inputs are outside the
+ * contract (results unspecified). */
+typedef enum {
+    ACCR_ADD = 0,
+    ACCR_MUL = 1,
+    ACCR_MAX = 2,
+    ACCR_MIN = 3,
+    ACCR_BAND = 4,
+    ACCR_BOR = 5,
+    ACCR_BXOR = 6,
+    ACCR_LAND = 7,
+    ACCR_LOR = 8
+} accr_op;
+
+/* Status codes. */
+#define ACCR_OK 0
+#define ACCR_EINVAL (-1)    /* bad pointer, size, alignment or flag */
+#define ACCR_ETYPE (-2)     /* operator undefined for the type, or narrowing */
+#define ACCR_ENOMEM (-3)    /* scratch allocation failed */
+#define ACCR_ECUDA (-4)     /* a CUDA call failed (message has the CUDA error) */
+#define ACCR_EAGAIN (-5)    /* result not ready yet (accr_poll) */
+#define ACCR_EBUDGET (-6)   /* region larger than the server's memory budget */
+#define ACCR_ETIMEDOUT (-7) /* a bounded wait ran out */
+
+/* Flags. */
+#define ACCR_COMPENSATED 0x1u   /* float + into a float variable: compensated
+                                   (Neumaier) sums per thread, pairwise TwoSum
+                                   combine, double-precision cross-gang merge */
+#define ACCR_SYNC 0x2u          /* return only after the result is written */
+#define ACCR_TWO_LEVEL_HOST 0x4u /* the paper's two-level form (SRAD in Sec. 4.2):
+                                   block partials on the GPU, copied to the
+                                   host and merged there; `out` is then a HOST
+                                   pointer and the call is synchronous */
+
+#define ACCR_MAX_CLAUSES 4
+
+/* One reduction(op:var) clause.  The accumulator type is the variable's type:
+ * integer elements need an integer variable at least as wide (int32 elements
+ * into an int64 variable are sign-extended); floating-point elements need a
+ * floating-point variable at least as wide. */
+typedef struct {
+    int32_t op;       /* accr_op */
+    int32_t acc_type; /* accr_type of the variable */
+    const void *init; /* HOST pointer to the variable's value before the
+                         region (read during the call), or NULL = identity */
+    void *out;        /* DEVICE pointer receiving the variable's value after
+                         the region (host pointer under ACCR_TWO_LEVEL_HOST) */
+} accr_clause;
+
+/*
+ * accr_reduce -- one region: a `loop independent` loop over i in [0, n) with
+ * 1..ACCR_MAX_CLAUSES reduction clauses evaluated in the same single pass
+ * (e.g. `reduction(+:s) reduction(max:m)`).
+ *
+ * Semantics (Stage 3.4 iii, Stage 3.7): for each clause,
+ *   var = init (op) x[0] (op) x[1] ... (op) x[n-1]
+ * where init is the variable's prior value.  Integer, bitwise, logical and
+ * min/max results are exact (any association gives the same bits).  Float +
+ * and * are evaluated in a fixed tree order (deterministic for a given device
+ * and n); n == 0 leaves the variable equal to init.
+ *
+ *   in        DEVICE, n elements of in_type
+ *   n         number of iterations (>= 0)
+ *   clauses   HOST array of nclauses clauses (1..ACCR_MAX_CLAUSES)
+ *   flags     ACCR_COMPENSATED | ACCR_SYNC | ACCR_TWO_LEVEL_HOST
+ *
+ * Device side: one persistent launch; each CTA folds its share into private
+ * accumulators, combines them through warp shuffles and shared memory, writes
+ * one partial per clause, and the last CTA to finish merges all partials in
+ * CTA order (a counter in library scratch, reset by that CTA).  Calls on
+ * different streams use different scratch and may overlap.
+ */
+ACCR_API int accr_reduce(const void *in, int64_t n, int32_t in_type,
+                const accr_clause *clauses, int32_t nclauses, uint32_t flags,
+                accr_stream_t stream);
+
+/*
+ * accr_rowreduce -- the nest `for i (gang) { for j (vector) var_i (op)= A[i][j] }`
+ * over a row-major matrix: out[i] = init (op) A[i*ld + 0] ... (op) A[i*ld + cols-1]
+ * for every row i < rows (the nest shape of Listing 1a with an inner
+ * reduction).  Each clause's `out` is a DEVICE array of `rows` variables; its
+ * `init` (if any) is the prior value of every row's variable.
+ *
+ *   A         DEVICE, rows x ld elements of in_type (ld >= cols)
+ *   flags     ACCR_COMPENSATED | ACCR_SYNC
+ */
+ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t ld,
+                   int32_t in_type, const accr_clause *clauses,
+                   int32_t nclauses, uint32_t flags, accr_stream_t stream);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+ACCR_API const char *accr_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+ACCR_API uint64_t accr_launch_count(void);
+
+/* ABI version of this header (major * 100 + minor). */
+ACCR_API int32_t accr_version(void);
+
+#define ACCR_VERSION 100
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,75 @@
+"""Loader of the in-tree C-ABI library ``libaccr.so`` (see ``include/accr.h``).
+
+There is no fallback: if the library is missing or does not load, every call
+raises, so no result can silently come from anywhere but the CUDA kernels.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaccr.so")
+
+# status codes of include/accr.h
+ACCR_OK = 0
+ACCR_EINVAL = -1
+ACCR_ETYPE = -2
+ACCR_ENOMEM = -3
+ACCR_ECUDA = -4
+ACCR_EAGAIN = -5
+ACCR_EBUDGET = -6
+ACCR_ETIMEDOUT = -7
+
+ERROR_NAMES = {ACCR_EINVAL: "EINVAL", ACCR_ETYPE: "ETYPE", ACCR_ENOMEM: "ENOMEM",
+               ACCR_ECUDA: "ECUDA", ACCR_EAGAIN: "EAGAIN", ACCR_EBUDGET: "EBUDGET",
+               ACCR_ETIMEDOUT: "ETIMEDOUT"}
+
+
+class AccrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Clause(ctypes.Structure):
+    """``accr_clause``: one reduction(op:var) clause."""
+    _fields_ = [("op", ctypes.c_int32), ("acc_type", ctypes.c_int32),
+                ("init", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+# Every symbol include/accr.h declares, with its ctypes signature.
+_vp, _i32, _i64, _u32, _u64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                               ctypes.c_uint32, ctypes.c_uint64)
+_CP = ctypes.POINTER(Clause)
+SIGNATURES = {
+    "accr_reduce": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
+    "accr_rowreduce": (ctypes.c_int, [_vp, _i64, _i64, _i64, _i32, _CP, _i32, _u32, _vp]),
+    "accr_last_error": (ctypes.c_char_p, []),
+    "accr_launch_count": (_u64, []),
+    "accr_version": (_i32, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libaccr.so is not built (run `python -c \"import __graft_entry__ as g; "
+                               "g.build()\"`); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    """Raise AccrError for a negative status."""
+    if rc != ACCR_OK:
+        msg = lib().accr_last_error()
+        raise AccrError(rc, msg.decode() if msg else "")
+    return rc

@@ -1,0 +1,74 @@
+"""accr_rowreduce (gang = row, vector = column) on the GPU against the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1412_1127_gb300 import api, inputs
+from tolerances import TOL_F32, TOL_F32_COMP, same_bits
+
+pytestmark = pytest.mark.gpu
+
+TD = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32, "f64": torch.float64}
+SHAPES = [(1, 1), (3, 5), (7, 33), (64, 128), (129, 1023), (1000, 4096), (5, 70001), (37, 0)]
+
+
+def gpu_rows(A_np, op, acc, init=None, flags=0, pad=0, offset=0):
+    rows, cols = A_np.shape
+    big = np.zeros((rows, cols + pad + offset), dtype=A_np.dtype)
+    big[:, offset:offset + cols] = A_np
+    t = torch.from_numpy(big).cuda()[:, offset:offset + cols]
+    out = torch.full((rows,), 9, dtype=TD[acc], device="cuda")
+    api.accr_rowreduce(t, [api.clause(op, out, init)], flags=flags)
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("op", ["add", "mul", "max", "min", "band", "bor", "bxor", "land", "lor"])
+def test_int_rows_bit_exact(shape, op):
+    g = np.random.default_rng(shape[0] * 7 + shape[1])
+    A = g.integers(-(1 << 31), 1 << 31, size=shape, dtype=np.int64).astype(np.int32)
+    if op == "land":
+        A |= 1
+        A[::3, -1:] = 0
+    for pad, off in [(0, 0), (3, 1)]:
+        assert np.array_equal(gpu_rows(A, op, "i64", pad=pad, offset=off), oracle.rowreduce(A, op, "i64"))
+        assert np.array_equal(gpu_rows(A, op, "i32", init=5, pad=pad, offset=off),
+                              oracle.rowreduce(A, op, "i32", init=5))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp_rows(shape):
+    A = inputs.uniform_matrix(*shape)
+    for op in ["max", "min"]:
+        for pad, off in [(0, 0), (5, 3)]:
+            assert same_bits(gpu_rows(A, op, "f32", pad=pad, offset=off), oracle.rowreduce(A, op))
+    rows, cols = shape
+    for flags, tol in [(0, TOL_F32), (api.ACCR_COMPENSATED, TOL_F32_COMP)]:
+        got = gpu_rows(A, "add", "f32", flags=flags, pad=1)
+        for r in range(rows):
+            truth = oracle.truth_sum(A[r])
+            err = abs(float(got[r]) - truth) / max(abs(truth), 0.1 * math.sqrt(max(cols, 1)) * 0.577)
+            assert err <= tol, (r, got[r], truth)
+    D = A.astype(np.float64)
+    got = gpu_rows(D, "add", "f64")
+    for r in range(rows):
+        truth = oracle.truth_sum(D[r])
+        assert abs(got[r] - truth) <= 1e-12 * max(abs(truth), 0.1 * math.sqrt(max(cols, 1)))
+
+
+def test_two_clauses_rows_full_size():
+    # row sum and row max of a 65536 x 4096 U(-1,1) float matrix in one pass
+    A = inputs.uniform_matrix(65536, 4096)
+    At = torch.from_numpy(A).cuda()
+    s = torch.empty(65536, dtype=torch.float32, device="cuda")
+    m = torch.empty(65536, dtype=torch.float32, device="cuda")
+    api.accr_rowreduce(At, [api.clause("add", s), api.clause("max", m)])
+    m_np, s_np = m.cpu().numpy(), s.cpu().numpy()
+    assert same_bits(m_np, oracle.rowreduce(A, "max"))
+    idx = np.random.default_rng(0).choice(65536, size=64, replace=False)
+    for r in idx:
+        truth = oracle.truth_sum(A[r])
+        assert abs(float(s_np[r]) - truth) / max(abs(truth), 0.1 * 64 * 0.577) <= TOL_F32
