@@ -218,7 +218,7 @@ def run_scalar(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    n = N_SCALAR
+    n = args.n
     host = make_scalar_inputs(n, rank)
     devin = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
     td = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32, "f64": torch.float64}
@@ -284,7 +284,7 @@ def run_scalar(args):
 
     # end to end through the public API: host (pinned) inputs copied in every step
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
         res_host = torch.empty(R, dtype=torch.int64).pin_memory()
 
@@ -332,8 +332,9 @@ def run_scalar(args):
             "vs_baseline": None,
             "dtype": "i32+i64+f32+f64",
             "data": "synthetic",
-            "config": {"workload": "all-operator scalar reduction, n=2^28 (16 regions: int32 "
-                                   "+,*,max,min,&,|,^,&&,||; float +,+comp,max,min; double +,max,min)",
+            "config": {"workload": "all-operator scalar reduction, n=%s (16 regions: int32 "
+                                   "+,*,max,min,&,|,^,&&,||; float +,+comp,max,min; double +,max,min)"
+                                   % ("2^%d" % int(math.log2(n)) if n & (n - 1) == 0 else str(n)),
                        "n": n, "regions_per_step": R, "bytes_per_step": bytes_step,
                        "l2": "inputs larger than L2 (1-2 GiB per region vs 129 MB); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -365,6 +366,9 @@ def main():
     ap.add_argument("--impl", default="accr", choices=["accr", "reference"])
     ap.add_argument("--workload", default="scalar", choices=["scalar"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=N_SCALAR,
+                    help="elements per region (default 2^28; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
