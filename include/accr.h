@@ -147,6 +147,36 @@ ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t l
                    int32_t in_type, const accr_clause *clauses,
                    int32_t nclauses, uint32_t flags, accr_stream_t stream);
 
+/*
+ * accr_reduce_noalloc -- accr_reduce without any device allocation.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- processes that hand all device memory to their own pool
+ * or arena up front, and latency-sensitive loops that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree can cause.
+ *
+ * Same arguments and results as accr_reduce (same grid, so the same bits),
+ * except that the block partials and the counter live in one fixed array of
+ * ACCR_NOALLOC_SCRATCH_BYTES (+256) bytes compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  A region
+ * whose nclauses x blocks x 16 bytes exceeds that size is rejected with
+ * ACCR_EINVAL (on a 152-SM GB300 the largest need is about 40 KB).
+ *
+ *   flags     ACCR_COMPENSATED | ACCR_SYNC (ACCR_TWO_LEVEL_HOST needs a pinned
+ *             host buffer and is rejected with ACCR_EINVAL)
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call clears the counter on `stream` before
+ * its launch.  All calls share the one array: calls that overlap on the GPU
+ * (different streams or threads) race on it and give wrong results, so
+ * serialise them.  Allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ */
+#define ACCR_NOALLOC_SCRATCH_BYTES 65536
+ACCR_API int accr_reduce_noalloc(const void *in, int64_t n, int32_t in_type,
+                                 const accr_clause *clauses, int32_t nclauses,
+                                 uint32_t flags, accr_stream_t stream);
+
 /* Message of the last error raised on the calling thread ("" if none). */
 ACCR_API const char *accr_last_error(void);
 

@@ -43,6 +43,7 @@ _CP = ctypes.POINTER(Clause)
 SIGNATURES = {
     "accr_reduce": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_rowreduce": (ctypes.c_int, [_vp, _i64, _i64, _i64, _i32, _CP, _i32, _u32, _vp]),
+    "accr_reduce_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_last_error": (ctypes.c_char_p, []),
     "accr_launch_count": (_u64, []),
     "accr_version": (_i32, []),

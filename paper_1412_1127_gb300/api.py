@@ -89,6 +89,20 @@ def accr_reduce(x, clauses, flags=0, stream=None, n=None):
                                    len(clauses), flags, _stream(stream)))
 
 
+def accr_reduce_noalloc(x, clauses, flags=0, stream=None, n=None):
+    """accr_reduce for callers that cannot allocate device memory: the block
+    partials and counter live in a fixed array inside the library.  Calls
+    that overlap on the GPU race on that array; serialise them."""
+    assert x.is_cuda and x.dim() == 1 and (x.stride(0) == 1 or x.numel() <= 1)
+    n = x.numel() if n is None else n
+    assert 0 <= n <= x.numel()
+    for c in clauses:
+        assert c.out.is_cuda and c.out.numel() >= 1
+    arr, keep = _clauses(clauses)
+    return check(lib().accr_reduce_noalloc(x.data_ptr() if x.numel() else None, n, type_of(x.dtype),
+                                           arr, len(clauses), flags, _stream(stream)))
+
+
 def accr_rowreduce(A, clauses, flags=0, stream=None):
     """Row nest: out[i] = fold of row i of the 2-D CUDA tensor A (rows may be
     padded: A may be a column slice of a wider row-major matrix)."""
