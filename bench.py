@@ -193,7 +193,8 @@ def run_reference(args):
         oracle_step(host, SCALAR_REGIONS, sample)
     dt = (time.perf_counter() - t0) / args.steps
     v = bytes_step / dt / 1e9
-    line = {"impl": "reference", "metric": "reduction GB/s (% of HBM peak)", "value": round(v, 4),
+    line = {"impl": "reference",
+            "metric": "reduction GB/s (% of HBM peak); batched regions/sec + p50/p99 latency vs plain", "value": round(v, 4),
             "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32+i64+f32+f64", "data": "synthetic",
@@ -318,9 +319,19 @@ def run_scalar(args):
                "sample": "first 2^26 elements of each of the 16 regions (1/4 of a step), serial C",
                "seconds": round(dt, 2)}
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        del devin, host
+        torch.cuda.empty_cache()
+        from paper_1412_1127_gb300 import autotune
+        autotune.load()
+        extra["batched"] = measure_batched(dev, max(3, min(args.steps, 10)), 3)
+        torch.cuda.empty_cache()
+        extra["served"] = measure_served(dev, args.served_seconds, args.rate)
+
     if rank == 0:
         line = {
-            "metric": "reduction GB/s (% of HBM peak)",
+            "metric": "reduction GB/s (% of HBM peak); batched regions/sec + p50/p99 latency vs plain",
             "value": round(value, 2),
             "unit": "GB/s",
             "n_gpus": world,
@@ -351,10 +362,186 @@ def run_scalar(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def build_batched(dev, count=20000):
+    """The many-regions workload on the device: 20,000 regions of log-uniform
+    length on [1, 2^20]; even ones float N(0,1) with compensated +, odd ones
+    int64 with + and ^ (two clauses, one pass)."""
+    import torch
+    from paper_1412_1127_gb300 import api, inputs
+    lengths, pf, off_f, pi, off_i = inputs.batched_regions(count)
+    tf, ti = torch.from_numpy(pf).to(dev), torch.from_numpy(pi).to(dev)
+    nf, ni = len(off_f) - 1, len(off_i) - 1
+    sf = torch.empty(nf, dtype=torch.float32, device=dev)
+    si = torch.empty(ni, dtype=torch.int64, device=dev)
+    xi = torch.empty(ni, dtype=torch.int64, device=dev)
+    regions = []
+    for k in range(len(lengths)):
+        j = k // 2
+        if k % 2 == 0:
+            regions.append((tf[off_f[j]:off_f[j + 1]], [api.clause("add", sf[j:j + 1])], api.ACCR_COMPENSATED))
+        else:
+            regions.append((ti[off_i[j]:off_i[j + 1]], [api.clause("add", si[j:j + 1]),
+                                                        api.clause("bxor", xi[j:j + 1])], 0))
+    nbytes = int(off_f[-1]) * 4 + int(off_i[-1]) * 8
+    return regions, nbytes, (sf, si, xi), (pf, off_f, pi, off_i)
+
+
+def measure_batched(dev, steps, warmup, count=20000, tune=False):
+    """regions/s and GB/s of the prepared (graph) batch, the one-shot batch and
+    the plain one-launch-per-region form, on the same regions."""
+    import torch
+    from paper_1412_1127_gb300 import api
+    regions, nbytes, outs, host = build_batched(dev, count)
+    R = len(regions)
+    tuned = None
+    if tune:
+        from paper_1412_1127_gb300 import autotune
+        best, res = autotune.tune(regions)
+        autotune.apply(*best)
+        tuned = {"best": list(best), "ms": {"%d,%d" % k: round(v, 4) for k, v in sorted(res.items())}}
+    stream = torch.cuda.current_stream(dev)
+    arr, keep = api.regions_array(regions)
+    L = api.lib()
+    b = api.Batch(regions)
+
+    def timed(fn, k):
+        for _ in range(max(warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = api.accr_launch_count()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k, (api.accr_launch_count() - l0) / k
+
+    ms_graph, lg = timed(lambda: b.launch(stream), steps)
+    res_graph = [o.clone() for o in outs]
+    ms_once, lo = timed(lambda: api.check(L.accr_batch_reduce(arr, R, 0, stream.cuda_stream)), steps)
+    ms_plain, lp = timed(lambda: api.check(L.accr_batch_reduce(arr, R, api.ACCR_PLAIN, stream.cuda_stream)),
+                         max(2, steps // 5))
+    res_plain = [o.clone() for o in outs]
+    same_int = bool(torch.equal(res_graph[1], res_plain[1]) and torch.equal(res_graph[2], res_plain[2]))
+    rel = ((res_graph[0].double() - res_plain[0].double()).abs()
+           / res_plain[0].double().abs().clamp_min(1e-3)).max().item()
+    b.destroy()
+    return {
+        "workload": "20,000 regions, lengths log-uniform [1, 2^20]: float N(0,1) compensated + / "
+                    "int64 + and ^ (alternating), %d elements, %.2f GB" % (
+                        int(host[1][-1] + host[3][-1]), nbytes / 1e9),
+        "regions": R,
+        "batched_graph": {"ms": round(ms_graph, 4), "regions_per_s": round(R / (ms_graph * 1e-3), 1),
+                          "gbs": round(nbytes / (ms_graph * 1e-3) / 1e9, 1), "launches": lg},
+        "batched_oneshot": {"ms": round(ms_once, 4), "regions_per_s": round(R / (ms_once * 1e-3), 1),
+                            "gbs": round(nbytes / (ms_once * 1e-3) / 1e9, 1), "launches": lo},
+        "plain": {"ms": round(ms_plain, 4), "regions_per_s": round(R / (ms_plain * 1e-3), 1),
+                  "gbs": round(nbytes / (ms_plain * 1e-3) / 1e9, 1), "launches": lp},
+        "speedup_vs_plain": round(ms_plain / ms_graph, 2),
+        "int_results_equal_plain": same_int,
+        "float_max_rel_diff_vs_plain": rel,
+        "tiling": list(api.accr_batch_tiling()),
+        "autotune": tuned,
+    }
+
+
+SERVED_CLAUSES = {"f32": [("add", "f32")], "i32": [("add", "i64"), ("max", "i32")],
+                  "i64": [("add", "i64"), ("bxor", "i64")]}
+
+
+def build_served(dev, count, rate, seed=5):
+    """The served workload: Poisson arrivals at `rate` regions/s; each region
+    is float32 (compensated +), int32 (+ into int64 and max) or int64 (+ and ^)
+    with length log-uniform on [2^8, 2^26], at a random offset of a resident
+    pool of its type (2^29 float32, 2^29 int32, 2^28 int64: 6 GiB)."""
+    import torch
+    from paper_1412_1127_gb300 import api, inputs
+    sizes = {"f32": 1 << 29, "i32": 1 << 29, "i64": 1 << 28}
+    host = {"f32": inputs.normal(sizes["f32"], np.float32, seed=seed, salt=1),
+            "i32": inputs.full_range_i32(sizes["i32"], seed=seed, salt=2),
+            "i64": inputs.uniform_i64(sizes["i64"], -(1 << 40), 1 << 40, seed=seed, salt=3)}
+    pools = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    g = inputs.rng(seed, 9)
+    lengths = inputs.log_uniform_lengths(count, 1 << 8, 1 << 26, seed=seed, salt=4)
+    kinds = g.integers(0, 3, size=count)
+    td = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32}
+    proto = {t: [api.clause(op, torch.empty(1, dtype=td[a], device=dev)) for op, a in c]
+             for t, c in SERVED_CLAUSES.items()}
+    regions, nbytes, meta = [], 0, []
+    for k in range(count):
+        t = ["f32", "i32", "i64"][int(kinds[k])]
+        n = int(lengths[k])
+        off = int(g.integers(0, sizes[t] - n))
+        regions.append((pools[t][off:off + n], proto[t], api.ACCR_COMPENSATED if t == "f32" else 0))
+        nbytes += n * (8 if t == "i64" else 4)
+        meta.append((t, off, n))
+    arrivals = inputs.poisson_arrivals(rate, count, seed=seed, salt=5)
+    return regions, arrivals, nbytes, meta, host, pools
+
+
+def latency_stats(res, n):
+    lat = np.array([res[i].done_ns - res[i].submit_ns for i in range(n)], dtype=np.float64) / 1e3
+    first = min(res[i].submit_ns for i in range(n))
+    last = max(res[i].done_ns for i in range(n))
+    return {"regions_per_s": round(n / ((last - first) * 1e-9), 1),
+            "p50_us": round(float(np.percentile(lat, 50)), 2),
+            "p99_us": round(float(np.percentile(lat, 99)), 2),
+            "p999_us": round(float(np.percentile(lat, 99.9)), 2),
+            "mean_us": round(float(lat.mean()), 2)}
+
+
+def measure_served(dev, seconds=2.0, rate=50000.0):
+    """Served regions/s and p50/p99 latency (arrival -> result visible on the
+    host) of the continuous-batching server against sequential plain launches,
+    on the same open-loop Poisson schedule."""
+    import torch
+    from paper_1412_1127_gb300 import api
+    count = int(seconds * rate)
+    regions, arrivals, nbytes, meta, host, pools = build_served(dev, count, rate)
+    srv = api.Server(64 << 30, nstreams=4, max_batch=4096)
+    warm = min(2000, count)
+    srv.replay(regions[:warm], arrivals[:warm])
+    res = srv.replay(regions, arrivals)
+    srv.destroy()
+    api.accr_server_replay(None, regions[:warm], arrivals[:warm], plain=True)
+    resp = api.accr_server_replay(None, regions, arrivals, plain=True)
+    st_s, st_p = latency_stats(res, count), latency_stats(resp, count)
+    # results: served and plain agree bit for bit on the integer regions
+    same = all(list(res[i].value[:res[i].nclauses]) == list(resp[i].value[:resp[i].nclauses])
+               for i in range(count) if meta[i][0] != "f32")
+    del pools
+    torch.cuda.empty_cache()
+    return {"workload": "served regions: Poisson arrivals at %d/s for %.1f s (%d regions, %.1f GB), lengths "
+                        "log-uniform [2^8, 2^26], float32 (+comp) / int32 (+, max) / int64 (+, ^), "
+                        "resident pools, 64 GiB budget, 4 stream slots" % (rate, seconds, count, nbytes / 1e9),
+            "offered_gbs": round(nbytes / arrivals[-1] / 1e9, 1),
+            "server": st_s, "plain_sequential": st_p,
+            "p99_speedup_vs_plain": round(st_p["p99_us"] / st_s["p99_us"], 2),
+            "int_results_equal_plain": bool(same)}
+
+
+def run_served(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_served(torch.device("cuda", 0), args.served_seconds, args.rate)), flush=True)
+    return 0
+
+
+def run_batched(args):
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    r = measure_batched(torch.device("cuda", 0), args.steps, args.warmup, args.regions, args.tune)
+    print(json.dumps(r), flush=True)
     return 0
 
 
@@ -364,9 +551,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="accr", choices=["accr", "reference"])
-    ap.add_argument("--workload", default="scalar", choices=["scalar"])
+    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served"])
+    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--rate", type=float, default=50000.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="scalar workload only (skip the batched and served sub-measurements)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--regions", type=int, default=20000, help="regions of the batched workload")
+    ap.add_argument("--tune", action="store_true", help="batched: autotune the split first")
     ap.add_argument("--n", type=int, default=N_SCALAR,
                     help="elements per region (default 2^28; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -374,6 +567,10 @@ def main():
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_scalar(args)
 
 

@@ -91,6 +91,8 @@ typedef enum {
                                    host and merged there; `out` is then a HOST
                                    pointer and the call is synchronous */
 
+#define ACCR_PLAIN 0x8u          /* accr_batch_reduce: one launch per region */
+
 #define ACCR_MAX_CLAUSES 4
 
 /* One reduction(op:var) clause.  The accumulator type is the variable's type:
@@ -146,6 +148,149 @@ ACCR_API int accr_reduce(const void *in, int64_t n, int32_t in_type,
 ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t ld,
                    int32_t in_type, const accr_clause *clauses,
                    int32_t nclauses, uint32_t flags, accr_stream_t stream);
+
+/* One region of a batch: the loop over in[0, n) with its own clauses.  Each
+ * clause's `out` is the DEVICE address of this region's variable. */
+typedef struct {
+    const void *in;    /* DEVICE, n elements of in_type */
+    int64_t n;         /* >= 0 */
+    int32_t in_type;   /* accr_type */
+    int32_t nclauses;  /* 1..ACCR_MAX_CLAUSES */
+    uint32_t flags;    /* ACCR_COMPENSATED or 0 */
+    int32_t reserved;  /* 0 */
+    accr_clause clauses[ACCR_MAX_CLAUSES];
+} accr_region;
+
+/* A prepared batch (see accr_batch_create). */
+typedef struct accr_batch accr_batch;
+
+/*
+ * accr_batch_reduce -- many independent regions, each with the semantics of
+ * accr_reduce, in ONE persistent launch.  This removes the per-region launch
+ * cost that the paper's time breakdown charges to every kernel call
+ * (Methodology: cudaLaunch, cudaSetupArgument, cudaConfigureCall).
+ *
+ * Work split: a region of at most ACCR_SMALL_BYTES (by default) is folded
+ * whole by one warp; a longer region is cut into tiles of ACCR_TILE_BYTES (by
+ * default) that CTAs fold independently; the last tile of a region to finish
+ * merges the region's tile partials in tile order and writes its variables.
+ * The split depends only on each region's own type and length, so a region
+ * gives the same bits alone and inside any batch.  A region with three or
+ * four clauses is run as two halves (clauses 0-1, 2-3) that each read its
+ * elements.
+ *
+ *   regions   HOST array of nregions descriptors (read during the call; the
+ *             `init` values are read then too)
+ *   flags     ACCR_SYNC | ACCR_PLAIN (ACCR_PLAIN: the unbatched form, one
+ *             accr_reduce launch per region in order, as the comparison point)
+ */
+ACCR_API int accr_batch_reduce(const accr_region *regions, int64_t nregions,
+                               uint32_t flags, accr_stream_t stream);
+
+/*
+ * accr_segmented_reduce -- regions that share one element array, element type
+ * and clause list: segment s is values[offsets[s] .. offsets[s+1]).  Each
+ * clause's `out` is a DEVICE array of nseg variables; `init` (if any) is the
+ * prior value of every segment's variable.  Same device path as
+ * accr_batch_reduce.
+ *
+ *   values    DEVICE array of in_type
+ *   offsets   HOST array of nseg+1 non-decreasing element offsets (loop bounds
+ *             are host values, as in Listing 1a)
+ *   flags     ACCR_COMPENSATED | ACCR_SYNC
+ */
+ACCR_API int accr_segmented_reduce(const void *values, const int64_t *offsets,
+                                   int64_t nseg, int32_t in_type,
+                                   const accr_clause *clauses, int32_t nclauses,
+                                   uint32_t flags, accr_stream_t stream);
+
+/*
+ * accr_batch_create / accr_batch_launch / accr_batch_destroy -- a batch that
+ * is run many times.  Create plans the tiles, uploads the plan to device
+ * memory owned by the batch, and captures the persistent launch in a CUDA
+ * graph; launch replays that graph on `stream` (one graph launch, no host
+ * planning, no upload); destroy waits for the batch's work and frees it.
+ * The descriptors (pointers, lengths, clauses, init values) are fixed at
+ * create time.  Launches of one batch must not overlap on the GPU (they share
+ * the batch's tile partials).
+ */
+ACCR_API int accr_batch_create(const accr_region *regions, int64_t nregions,
+                               uint32_t flags, accr_batch **batch);
+ACCR_API int accr_batch_launch(accr_batch *batch, accr_stream_t stream);
+ACCR_API int accr_batch_destroy(accr_batch *batch);
+
+/* Tiling of batched regions, process-wide: regions of at most small_bytes are
+ * folded by one warp, longer ones in tiles of tile_bytes (both multiples of
+ * 16, tile_bytes >= 4096).  Changing it changes the evaluation order of float
+ * sums (every later call uses the new split).  Returns the previous values
+ * through the pointers when they are not NULL; 0 keeps a value. */
+ACCR_API int accr_batch_tiling(int64_t small_bytes, int64_t tile_bytes,
+                               int64_t *old_small, int64_t *old_tile);
+#define ACCR_SMALL_BYTES 65536
+#define ACCR_TILE_BYTES 2097152
+
+/* ---- served request loop ---------------------------------------------------- */
+
+/* A request loop that takes regions as they arrive and runs them in
+ * continuous batches (see accr_server_create). */
+typedef struct accr_server accr_server;
+
+/* Result of one served region. */
+typedef struct {
+    int32_t status;                     /* ACCR_OK or the error of its batch */
+    int32_t nclauses;
+    uint64_t value[ACCR_MAX_CLAUSES];   /* each variable's bits (4-byte types
+                                           in the low half) */
+    int64_t submit_ns;                  /* steady-clock times: accepted, */
+    int64_t launch_ns;                  /* its batch launched, */
+    int64_t done_ns;                    /* result visible to the host */
+} accr_result;
+
+/*
+ * accr_server_create -- start a request loop on the current device.
+ *
+ * Regions submitted with accr_submit wait in a FIFO queue.  A region is
+ * admitted when the bytes of all admitted-but-unfinished regions plus its
+ * own stay within `hbm_budget_bytes` (the arrays stay resident on the device;
+ * the budget bounds how much of them is in flight).  A scheduler thread
+ * forms a batch of up to `max_batch` admitted regions whenever one of
+ * `nstreams` stream slots is free and launches it with the batched-region
+ * kernel (accr_batch_reduce); batches on different slots overlap on the GPU,
+ * and regions that arrive while batches run form the next batch.  Each
+ * region's variables come back to the host with its batch.  A region's
+ * result does not depend on which batch it ran in.
+ */
+ACCR_API int accr_server_create(uint64_t hbm_budget_bytes, int32_t nstreams,
+                                int32_t max_batch, accr_server **server);
+
+/* Queue one region (`clauses[c].out` is ignored: results come back through
+ * accr_poll).  Returns ACCR_EBUDGET if the region alone exceeds the budget.
+ * The descriptor is copied; the region's elements must stay valid until its
+ * result has been polled. */
+ACCR_API int accr_submit(accr_server *server, const accr_region *region,
+                         uint64_t *ticket);
+
+/* Result of `ticket`: timeout_us == 0 returns ACCR_EAGAIN at once if it is
+ * not ready; timeout_us > 0 waits at most that long (then ACCR_ETIMEDOUT);
+ * timeout_us < 0 waits until it is ready.  A result is returned once. */
+ACCR_API int accr_poll(accr_server *server, uint64_t ticket, accr_result *out,
+                       int64_t timeout_us);
+
+/* Drain the queue, stop the scheduler and free the server. */
+ACCR_API int accr_server_destroy(accr_server *server);
+
+/*
+ * accr_server_replay -- an open-loop client for measurement: submits
+ * regions[i] at arrival_s[i] seconds after the call starts (in order, waiting
+ * on the steady clock), then collects every result into results[i].  With
+ * ACCR_PLAIN in `flags` the server is bypassed: each region runs as one
+ * synchronous accr_reduce on `stream` at (or after) its arrival time -- the
+ * sequential plain-launch comparison.  `server` may be NULL with ACCR_PLAIN.
+ */
+ACCR_API int accr_server_replay(accr_server *server, const accr_region *regions,
+                                const double *arrival_s, int64_t n,
+                                uint32_t flags, accr_stream_t stream,
+                                accr_result *results);
 
 /*
  * accr_reduce_noalloc -- accr_reduce without any device allocation.  The

@@ -36,6 +36,20 @@ class Clause(ctypes.Structure):
                 ("init", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
+class Region(ctypes.Structure):
+    """``accr_region``: one region of a batch."""
+    _fields_ = [("in_", ctypes.c_void_p), ("n", ctypes.c_int64), ("in_type", ctypes.c_int32),
+                ("nclauses", ctypes.c_int32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("clauses", Clause * 4)]
+
+
+class Result(ctypes.Structure):
+    """``accr_result``: one served region's variables and times."""
+    _fields_ = [("status", ctypes.c_int32), ("nclauses", ctypes.c_int32),
+                ("value", ctypes.c_uint64 * 4), ("submit_ns", ctypes.c_int64),
+                ("launch_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
 # Every symbol include/accr.h declares, with its ctypes signature.
 _vp, _i32, _i64, _u32, _u64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                ctypes.c_uint32, ctypes.c_uint64)
@@ -43,6 +57,18 @@ _CP = ctypes.POINTER(Clause)
 SIGNATURES = {
     "accr_reduce": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_rowreduce": (ctypes.c_int, [_vp, _i64, _i64, _i64, _i32, _CP, _i32, _u32, _vp]),
+    "accr_batch_reduce": (ctypes.c_int, [ctypes.POINTER(Region), _i64, _u32, _vp]),
+    "accr_segmented_reduce": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _i64, _i32, _CP, _i32, _u32, _vp]),
+    "accr_batch_create": (ctypes.c_int, [ctypes.POINTER(Region), _i64, _u32, ctypes.POINTER(_vp)]),
+    "accr_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "accr_batch_destroy": (ctypes.c_int, [_vp]),
+    "accr_batch_tiling": (ctypes.c_int, [_i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "accr_server_create": (ctypes.c_int, [_u64, _i32, _i32, ctypes.POINTER(_vp)]),
+    "accr_submit": (ctypes.c_int, [_vp, ctypes.POINTER(Region), ctypes.POINTER(_u64)]),
+    "accr_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(Result), _i64]),
+    "accr_server_destroy": (ctypes.c_int, [_vp]),
+    "accr_server_replay": (ctypes.c_int, [_vp, ctypes.POINTER(Region), ctypes.POINTER(ctypes.c_double), _i64,
+                                          _u32, _vp, ctypes.POINTER(Result)]),
     "accr_reduce_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_last_error": (ctypes.c_char_p, []),
     "accr_launch_count": (_u64, []),

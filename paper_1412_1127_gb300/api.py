@@ -13,8 +13,10 @@ from ._native import Clause, check, lib
 
 ACCR_I32, ACCR_I64, ACCR_F32, ACCR_F64 = 0, 1, 2, 3
 ACCR_ADD, ACCR_MUL, ACCR_MAX, ACCR_MIN, ACCR_BAND, ACCR_BOR, ACCR_BXOR, ACCR_LAND, ACCR_LOR = range(9)
-ACCR_COMPENSATED, ACCR_SYNC, ACCR_TWO_LEVEL_HOST = 0x1, 0x2, 0x4
+ACCR_COMPENSATED, ACCR_SYNC, ACCR_TWO_LEVEL_HOST, ACCR_PLAIN = 0x1, 0x2, 0x4, 0x8
 ACCR_MAX_CLAUSES = 4
+ACCR_SMALL_BYTES = 65536   # default split of batched regions (include/accr.h)
+ACCR_TILE_BYTES = 2097152
 
 OPS = {"add": ACCR_ADD, "mul": ACCR_MUL, "max": ACCR_MAX, "min": ACCR_MIN, "band": ACCR_BAND,
        "bor": ACCR_BOR, "bxor": ACCR_BXOR, "land": ACCR_LAND, "lor": ACCR_LOR,
@@ -114,6 +116,177 @@ def accr_rowreduce(A, clauses, flags=0, stream=None):
     arr, keep = _clauses(clauses)
     return check(lib().accr_rowreduce(A.data_ptr() if A.numel() else None, rows, cols, max(ld, cols),
                                       type_of(A.dtype), arr, len(clauses), flags, _stream(stream)))
+
+
+def _region_desc(x, clauses, flags, keep):
+    return _region(x, clauses, flags, keep, need_out=False)
+
+
+def _region(x, clauses, flags, keep, need_out=True):
+    assert x.is_cuda and x.dim() == 1 and (x.stride(0) == 1 or x.numel() <= 1)
+    assert 1 <= len(clauses) <= ACCR_MAX_CLAUSES
+    g = _native.Region()
+    g.in_ = x.data_ptr() if x.numel() else None
+    g.n = x.numel()
+    g.in_type = type_of(x.dtype)
+    g.nclauses = len(clauses)
+    g.flags = flags
+    g.reserved = 0
+    for i, c in enumerate(clauses):
+        if need_out:
+            assert c.out.is_cuda and c.out.numel() >= 1
+        g.clauses[i] = c._c(keep)
+    return g
+
+
+def regions_array(regions, need_out=True):
+    """ctypes array of ``accr_region`` from (tensor, [clause...], flags) triples."""
+    keep = []
+    arr = (_native.Region * max(len(regions), 1))()
+    for i, (x, cls, fl) in enumerate(regions):
+        arr[i] = _region(x, cls, fl, keep, need_out)
+    return arr, keep
+
+
+def accr_batch_reduce(regions, flags=0, stream=None):
+    """Many independent regions in one launch.  `regions` is a list of
+    (1-D CUDA tensor, [clause, ...], flags) triples; each clause's `out` is a
+    one-element CUDA tensor (or a one-element view into a larger one)."""
+    arr, keep = regions_array(regions)
+    return check(lib().accr_batch_reduce(arr, len(regions), flags, _stream(stream)))
+
+
+def accr_segmented_reduce(values, offsets, clauses, flags=0, stream=None):
+    """Segments values[offsets[s]:offsets[s+1]] of one CUDA tensor, one
+    variable per segment in each clause's `out` array (length nseg).
+    `offsets` is a host sequence of nseg + 1 element offsets."""
+    import numpy as np
+    assert values.is_cuda and values.dim() == 1 and (values.stride(0) == 1 or values.numel() <= 1)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nseg = off.size - 1
+    assert nseg >= 0 and (nseg == 0 or off[-1] <= values.numel())
+    for c in clauses:
+        assert c.out.is_cuda and c.out.numel() >= nseg
+    arr, keep = _clauses(clauses)
+    return check(lib().accr_segmented_reduce(
+        values.data_ptr() if values.numel() else None,
+        off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nseg, type_of(values.dtype), arr,
+        len(clauses), flags, _stream(stream)))
+
+
+class Batch:
+    """A prepared batch (accr_batch_create): launch() replays its CUDA graph."""
+
+    def __init__(self, regions):
+        arr, keep = regions_array(regions)
+        h = ctypes.c_void_p()
+        check(lib().accr_batch_create(arr, len(regions), 0, ctypes.byref(h)))
+        self.handle = h
+        self._tensors = [(x, [c.out for c in cls]) for x, cls, _ in regions]
+
+    def launch(self, stream=None):
+        return check(lib().accr_batch_launch(self.handle, _stream(stream)))
+
+    def destroy(self):
+        if self.handle:
+            check(lib().accr_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def accr_batch_create(regions):
+    return Batch(regions)
+
+
+def accr_batch_launch(batch, stream=None):
+    return batch.launch(stream)
+
+
+def accr_batch_destroy(batch):
+    return batch.destroy()
+
+
+def accr_batch_tiling(small_bytes=0, tile_bytes=0):
+    """Set the batched-region split (0 keeps a value); returns the old values."""
+    os_, ot = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().accr_batch_tiling(small_bytes, tile_bytes, ctypes.byref(os_), ctypes.byref(ot)))
+    return os_.value, ot.value
+
+
+class Server:
+    """The served request loop (accr_server_create ... accr_server_destroy)."""
+
+    def __init__(self, hbm_budget_bytes, nstreams=4, max_batch=1024):
+        h = ctypes.c_void_p()
+        check(lib().accr_server_create(int(hbm_budget_bytes), nstreams, max_batch, ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, x, clauses, flags=0):
+        """Queue one region over the CUDA tensor x; clauses give (op, variable
+        dtype) through `clause(op, out)` where only out's dtype is used."""
+        keep = []
+        g = _region_desc(x, clauses, flags, keep)
+        t = ctypes.c_uint64()
+        check(lib().accr_submit(self.handle, ctypes.byref(g), ctypes.byref(t)))
+        self._keep[t.value] = (x, keep)
+        return t.value
+
+    def poll(self, ticket, timeout_us=-1):
+        """(status, [values...]) of a ticket; values decoded by variable type."""
+        r = _native.Result()
+        rc = lib().accr_poll(self.handle, ticket, ctypes.byref(r), int(timeout_us))
+        if rc == _native.ACCR_EAGAIN or rc == _native.ACCR_ETIMEDOUT:
+            return rc, None, r
+        self._keep.pop(ticket, None)
+        check(rc)
+        return rc, list(r.value[: r.nclauses]), r
+
+    def replay(self, regions, arrival_s, plain=False, stream=None):
+        return accr_server_replay(self, regions, arrival_s, plain, stream)
+
+    def destroy(self):
+        if self.handle:
+            check(lib().accr_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def decode(bits, dtype):
+    """A variable's value from the 64-bit slot of an accr_result."""
+    import numpy as np
+    nd = {torch.int32: np.int32, torch.int64: np.int64, torch.float32: np.float32,
+          torch.float64: np.float64}[dtype]
+    b = np.array([bits], dtype=np.uint64)
+    if np.dtype(nd).itemsize == 4:
+        return b.astype(np.uint32).view(nd)[0]
+    return b.view(nd)[0]
+
+
+def accr_server_replay(server, regions, arrival_s, plain=False, stream=None):
+    """Open-loop client: region i is submitted at arrival_s[i] seconds after
+    the call starts; with plain=True each region instead runs as one
+    synchronous single-region launch (server may be None).  Returns the ctypes
+    array of accr_result (values decode with `decode`)."""
+    import numpy as np
+    arr, keep = regions_array(regions, need_out=False)
+    at = np.ascontiguousarray(np.asarray(arrival_s, dtype=np.float64))
+    assert at.size == len(regions)
+    res = (_native.Result * max(len(regions), 1))()
+    handle = server.handle if server is not None else None
+    check(lib().accr_server_replay(handle, arr, at.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   len(regions), ACCR_PLAIN if plain else 0, _stream(stream), res))
+    return res
 
 
 def accr_last_error():

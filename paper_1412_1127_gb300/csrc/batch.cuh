@@ -1,0 +1,11 @@
+// batch.cuh -- internal entry of the batched-region path for other parts of
+// the library (the served request loop).
+#pragma once
+
+#include "common.cuh"
+
+namespace accr {
+// Plans and launches `nregions` regions (the accr_batch_reduce device path)
+// on `stream`; variables go to the device addresses in the descriptors.
+int batch_launch_regions(const accr_region *regions, int64_t nregions, accr_stream_t stream);
+}  // namespace accr

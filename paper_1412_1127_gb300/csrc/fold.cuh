@@ -477,6 +477,31 @@ __device__ __forceinline__ void warp_merge(int w, bool elem64, Acc &A) {
     }
 }
 
+// Merge one accumulator per clause across a CTA of NT threads (all threads
+// call it); thread 0 ends with the totals.  `sh` is NC x NT/32 shared slots.
+template <int NC, int NT>
+__device__ __forceinline__ void cta_merge(const int (&w)[NC], const uint64_t (&ident)[NC], bool e64,
+                                          Acc (&A)[NC], Acc (*sh)[NT / 32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        warp_merge(w[c], e64, A[c]);
+        if (lane == 0) sh[c][warp] = A[c];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            Acc B;
+            if (lane < NT / 32) B = sh[c][lane];
+            else { B.a = ident[c]; B.c = 0.f; }
+            warp_merge(w[c], e64, B);
+            A[c] = B;
+        }
+    }
+    __syncthreads();
+}
+
 // The cross-gang merge of compensated sums runs in double: each (s, c) pair
 // becomes s + c in double and the doubles are added.
 __host__ __device__ __forceinline__ int final_code(int w) { return w == W_ADDF_COMP ? W_ADDF_WIDE : w; }

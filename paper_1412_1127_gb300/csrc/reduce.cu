@@ -52,30 +52,6 @@ __device__ __forceinline__ Partial ld_partial(const Partial *p) {
     return q;
 }
 
-// Merge one accumulator per clause across the CTA; thread 0 gets the totals.
-template <int NC, int NT>
-__device__ __forceinline__ void cta_merge(const int (&w)[NC], const uint64_t (&ident)[NC], bool e64,
-                                          Acc (&A)[NC], Acc (*sh)[NT / 32]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        warp_merge(w[c], e64, A[c]);
-        if (lane == 0) sh[c][warp] = A[c];
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            Acc B;
-            if (lane < NT / 32) B = sh[c][lane];
-            else { B.a = ident[c]; B.c = 0.f; }
-            warp_merge(w[c], e64, B);
-            A[c] = B;
-        }
-    }
-    __syncthreads();
-}
-
 template <typename T, int NC>
 __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ ReduceArgs p) {
     constexpr bool E64 = sizeof(T) == 8;

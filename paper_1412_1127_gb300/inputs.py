@@ -16,6 +16,7 @@ distributions of the workloads this library is measured on:
 * ``adversarial_i32``    int32 arrays whose reduction is not trivially 0 / -1
 * ``log_uniform_lengths``  region lengths log-uniform on [lo, hi]
 * ``poisson_arrivals``   open-loop arrival times for the served request loop
+* ``batched_regions``    20,000 regions of log-uniform length, float and int64
 """
 import numpy as np
 
@@ -120,3 +121,18 @@ def poisson_arrivals(rate_per_s, count, seed=5, salt=0):
     """Arrival times (seconds from 0) of an open-loop Poisson process."""
     g = rng(seed, salt)
     return np.cumsum(g.exponential(1.0 / rate_per_s, size=count))
+
+
+def batched_regions(count=20000, lo=1, hi=1 << 20, seed=4, salt=0):
+    """The many-regions workload: `count` regions with lengths log-uniform on
+    [lo, hi], in random order; even-numbered regions hold float32 N(0,1),
+    odd-numbered int64 uniform in [-2^40, 2^40].  Returns (lengths, f32 pool,
+    f32 offsets, i64 pool, i64 offsets): region 2k is segment k of the f32
+    pool, region 2k+1 segment k of the i64 pool."""
+    lengths = log_uniform_lengths(count, lo, hi, seed, salt)
+    lf, li = lengths[0::2], lengths[1::2]
+    off_f = offsets_from_lengths(lf)
+    off_i = offsets_from_lengths(li)
+    pool_f = normal(int(off_f[-1]), np.float32, seed=seed, salt=salt + 1)
+    pool_i = uniform_i64(int(off_i[-1]), -(1 << 40), 1 << 40, seed=seed, salt=salt + 2)
+    return lengths, pool_f, off_f, pool_i, off_i
