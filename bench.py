@@ -328,6 +328,8 @@ def run_scalar(args):
         extra["batched"] = measure_batched(dev, max(3, min(args.steps, 10)), 3)
         torch.cuda.empty_cache()
         extra["served"] = measure_served(dev, args.served_seconds, args.rate)
+        torch.cuda.empty_cache()
+        extra["matmul"] = measure_matmul(dev)
 
     if rank == 0:
         line = {
@@ -536,6 +538,54 @@ def run_served(args):
     return 0
 
 
+def measure_matmul(dev, length=4096, reps=5):
+    """The Listing-1 nest at LEN x LEN (U(-1,1) float): FP32 SIMT (fused and
+    serial-order) and BF16x3 tcgen05, TFLOP/s of 2*LEN^3 and the error of
+    sampled entries against the double-accumulated product."""
+    import torch
+    import oracle
+    from paper_1412_1127_gb300 import api, inputs
+    a = inputs.uniform_matrix(length, length, salt=41)
+    b = inputs.uniform_matrix(length, length, salt=42)
+    at, bt = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    ct = torch.empty_like(at)
+    stream = torch.cuda.current_stream(dev)
+    flops = 2.0 * length ** 3
+    peaks, kind = measured_peaks()
+    g = np.random.default_rng(0)
+    idx = list(zip(g.integers(0, length, 32), g.integers(0, length, 32)))
+    truth = [oracle.matmul_truth_at(a, b, int(i), int(j)) for i, j in idx]
+    out = {"workload": "Listing-1 nest, LEN=%d, float U(-1,1)" % length}
+    for mode in ["simt", "serial", "bf16x3"]:
+        for _ in range(2):
+            api.accr_matmul_nest(at, bt, ct, mode=mode, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            api.accr_matmul_nest(at, bt, ct, mode=mode, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        c = ct.cpu().numpy()
+        err = max(abs(float(c[i, j]) - t) / s_ for (i, j), (t, s_) in zip(idx, truth))
+        r = {"ms": round(ms, 4), "tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+             "max_err_over_sum_abs_products": err}
+        if mode == "bf16x3":
+            r["tensor_tflops"] = round(3 * flops / (ms * 1e-3) / 1e12, 2)
+            r["frac_of_bf16_peak"] = round(3 * flops / (ms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]), 4)
+            r["note"] = "time includes the two split kernels; tensor work is 3 products"
+        out[mode] = r
+    return out
+
+
+def run_matmul(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_matmul(torch.device("cuda", 0))), flush=True)
+    return 0
+
+
 def run_batched(args):
     import torch
     import __graft_entry__
@@ -551,7 +601,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="accr", choices=["accr", "reference"])
-    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served"])
+    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served", "matmul"])
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--rate", type=float, default=50000.0)
     ap.add_argument("--no-extra", action="store_true",
@@ -571,6 +621,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "matmul":
+        return run_matmul(args)
     return run_scalar(args)
 
 

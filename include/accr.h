@@ -149,6 +149,39 @@ ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t l
                    int32_t in_type, const accr_clause *clauses,
                    int32_t nclauses, uint32_t flags, accr_stream_t stream);
 
+/* ---- the Listing-1a nest ------------------------------------------------------ */
+
+#define ACCR_MM_SIMT 0        /* FP32 on CUDA cores, fused multiply-add */
+#define ACCR_MM_SIMT_SERIAL 1 /* FP32 on CUDA cores, each product rounded then
+                                 added, l in order: the serial program's bits */
+#define ACCR_MM_BF16X3 2      /* tensor cores (tcgen05), BF16x3 split precision */
+
+/*
+ * accr_matmul_nest -- Listing 1a (Sec. 1.3):
+ *   for i, j (independent):  c[i*len + j] = sum over l = 0..len-1 (in order)
+ *                                             of a[i*len + l] * b[l*len + j]
+ * with float inputs and a float accumulator.
+ *
+ *   a, b, c   DEVICE, len x len row-major float (4-byte aligned; 16-byte
+ *             aligned rows take the vector path)
+ *   mode      ACCR_MM_SIMT: tiled FP32 fused multiply-add (per output the l
+ *                 terms are still added in order); error at most about
+ *                 len * 2^-24 * sum_l |a_il b_lj|.
+ *             ACCR_MM_SIMT_SERIAL: the same tiling with the product rounded
+ *                 before the add: bit-identical to the serial float program.
+ *             ACCR_MM_BF16X3: each operand split into bf16 hi + lo, c =
+ *                 a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in FP32 in
+ *                 tensor memory (tcgen05.mma, TMA-fed); error of order 2^-16
+ *                 of sum_l |a_il b_lj| (the dropped lo*lo term and the split
+ *                 residuals).  Uses library scratch of 8 * len * ceil64(len)
+ *                 bytes per stream for the split operands.
+ *   flags     ACCR_SYNC (with ACCR_MM_BF16X3 also reports ACCR_ETIMEDOUT if
+ *             a pipeline wait inside the kernel ran out)
+ */
+ACCR_API int accr_matmul_nest(const float *a, const float *b, float *c,
+                              int64_t len, int32_t mode, uint32_t flags,
+                              accr_stream_t stream);
+
 /* One region of a batch: the loop over in[0, n) with its own clauses.  Each
  * clause's `out` is the DEVICE address of this region's variable. */
 typedef struct {

@@ -69,6 +69,7 @@ SIGNATURES = {
     "accr_server_destroy": (ctypes.c_int, [_vp]),
     "accr_server_replay": (ctypes.c_int, [_vp, ctypes.POINTER(Region), ctypes.POINTER(ctypes.c_double), _i64,
                                           _u32, _vp, ctypes.POINTER(Result)]),
+    "accr_matmul_nest": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _u32, _vp]),
     "accr_reduce_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_last_error": (ctypes.c_char_p, []),
     "accr_launch_count": (_u64, []),

@@ -289,6 +289,20 @@ def accr_server_replay(server, regions, arrival_s, plain=False, stream=None):
     return res
 
 
+ACCR_MM_SIMT, ACCR_MM_SIMT_SERIAL, ACCR_MM_BF16X3 = 0, 1, 2
+MM_MODES = {"simt": ACCR_MM_SIMT, "serial": ACCR_MM_SIMT_SERIAL, "bf16x3": ACCR_MM_BF16X3}
+
+
+def accr_matmul_nest(a, b, c, mode="simt", flags=0, stream=None):
+    """Listing 1a: c = a @ b for len x len row-major float CUDA tensors."""
+    n = a.shape[0]
+    for t in (a, b, c):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == (n, n)
+    m = MM_MODES[mode] if isinstance(mode, str) else int(mode)
+    return check(lib().accr_matmul_nest(a.data_ptr() if n else None, b.data_ptr() if n else None,
+                                        c.data_ptr() if n else None, n, m, flags, _stream(stream)))
+
+
 def accr_last_error():
     return lib().accr_last_error().decode()
 

@@ -1,0 +1,152 @@
+// matmul_simt.cu -- the Listing-1a nest on FP32 CUDA cores.
+//
+//   for i (gang, independent) for j (vector, independent)
+//     { float sum = 0; for l (serial) sum += a[i*LEN+l] * b[l*LEN+j]; c[i*LEN+j] = sum; }
+//
+// The paper's own CUDA version (Listing 1b) gives every thread one output and
+// reads a and b straight from global memory; Sec. 4.2 (Matrix Mul) notes that
+// the tiled CUDA SDK version, which stages tiles in shared memory and shares
+// them among a block's threads, is much faster.  This kernel is the tiled
+// form: a CTA computes a 128 x 128 block of c, stages 8-wide k slices of a
+// (transposed) and b in double-buffered shared memory, and every thread keeps
+// an 8 x 8 register block (two 4 x 4 quadrants 64 apart, so the 16-byte
+// shared-memory reads of a warp hit distinct banks or broadcast).
+//
+// Every output still sums its l terms in order 0..LEN-1.  Mode SERIAL rounds
+// each product and then each sum (no fused multiply-add), which is exactly
+// the serial float program, bit for bit; mode FMA fuses them (faster, and
+// closer to the exact product).
+#include <string.h>
+
+#include "common.cuh"
+
+namespace accr {
+
+constexpr int MT = 128;  // CTA tile (rows and columns of c)
+constexpr int KT = 8;    // k slice per stage
+constexpr int NTH = 256; // threads per CTA
+
+template <bool SERIAL>
+__device__ __forceinline__ float mac(float acc, float x, float y) {
+    if constexpr (SERIAL) return __fadd_rn(acc, __fmul_rn(x, y));
+    else return __fmaf_rn(x, y, acc);
+}
+
+template <bool SERIAL, bool VEC>
+__global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__restrict__ a, const float *__restrict__ b,
+                                                             float *__restrict__ c, int64_t len) {
+    __shared__ __align__(16) float As[2][KT][MT];  // a slice, transposed: As[k][row]
+    __shared__ __align__(16) float Bs[2][KT][MT];  // b slice: Bs[k][col]
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.y * MT, col0 = (int64_t)blockIdx.x * MT;
+
+    // loaders: a 128x8 slice = 256 float4 (one per thread: row tid>>1, k (tid&1)*4);
+    //          b 8x128 slice = 256 float4 (k tid>>5, col (tid&31)*4)
+    const int a_r = tid >> 1, a_k = (tid & 1) * 4;
+    const int b_k = tid >> 5, b_c = (tid & 31) * 4;
+
+    auto load_a = [&](int64_t k0, float4 &v) {
+        const int64_t r = row0 + a_r, k = k0 + a_k;
+        if (VEC && r < len && k + 3 < len) {
+            v = __ldg(reinterpret_cast<const float4 *>(a + r * len + k));
+        } else {
+            v.x = (r < len && k + 0 < len) ? a[r * len + k + 0] : 0.f;
+            v.y = (r < len && k + 1 < len) ? a[r * len + k + 1] : 0.f;
+            v.z = (r < len && k + 2 < len) ? a[r * len + k + 2] : 0.f;
+            v.w = (r < len && k + 3 < len) ? a[r * len + k + 3] : 0.f;
+        }
+    };
+    auto load_b = [&](int64_t k0, float4 &v) {
+        const int64_t k = k0 + b_k, cc = col0 + b_c;
+        if (VEC && k < len && cc + 3 < len) {
+            v = __ldg(reinterpret_cast<const float4 *>(b + k * len + cc));
+        } else {
+            v.x = (k < len && cc + 0 < len) ? b[k * len + cc + 0] : 0.f;
+            v.y = (k < len && cc + 1 < len) ? b[k * len + cc + 1] : 0.f;
+            v.z = (k < len && cc + 2 < len) ? b[k * len + cc + 2] : 0.f;
+            v.w = (k < len && cc + 3 < len) ? b[k * len + cc + 3] : 0.f;
+        }
+    };
+    auto store_tiles = [&](int buf, const float4 &va, const float4 &vb) {
+        As[buf][a_k + 0][a_r] = va.x;
+        As[buf][a_k + 1][a_r] = va.y;
+        As[buf][a_k + 2][a_r] = va.z;
+        As[buf][a_k + 3][a_r] = va.w;
+        *reinterpret_cast<float4 *>(&Bs[buf][b_k][b_c]) = vb;
+    };
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    float4 va, vb;
+    load_a(0, va);
+    load_b(0, vb);
+    store_tiles(0, va, vb);
+    __syncthreads();
+    const int64_t nk = (len + KT - 1) / KT;
+    for (int64_t kt = 0; kt < nk; ++kt) {
+        const int cur = (int)(kt & 1);
+        const bool more = kt + 1 < nk;
+        if (more) {  // fetch the next slice while this one is used
+            load_a((kt + 1) * KT, va);
+            load_b((kt + 1) * KT, vb);
+        }
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[cur][k][64 + tx * 4]);
+            const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = mac<SERIAL>(acc[i][j], ar[i], br[j]);
+        }
+        if (more) store_tiles(cur ^ 1, va, vb);
+        __syncthreads();
+    }
+    // write the 8 x 8 register block
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (r >= len) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t cc = col0 + h * 64 + tx * 4;
+            float4 v = make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
+            if (VEC && cc + 3 < len) {
+                *reinterpret_cast<float4 *>(c + r * len + cc) = v;
+            } else {
+                if (cc + 0 < len) c[r * len + cc + 0] = v.x;
+                if (cc + 1 < len) c[r * len + cc + 1] = v.y;
+                if (cc + 2 < len) c[r * len + cc + 2] = v.z;
+                if (cc + 3 < len) c[r * len + cc + 3] = v.w;
+            }
+        }
+    }
+}
+
+int matmul_simt(const float *a, const float *b, float *c, int64_t len, bool serial, cudaStream_t s) {
+    if (len == 0) return ACCR_OK;
+    const int64_t tiles = (len + MT - 1) / MT;
+    if (tiles > 65535) return set_error(ACCR_EINVAL, "accr_matmul_nest: len too large for the SIMT grid");
+    dim3 grid((unsigned)tiles, (unsigned)tiles);
+    // 16-byte vector access needs 16-byte aligned rows
+    const bool vec = (len % 4 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) && ((uintptr_t)c % 16 == 0);
+    if (serial) {
+        if (vec) matmul_simt_kernel<true, true><<<grid, NTH, 0, s>>>(a, b, c, len);
+        else matmul_simt_kernel<true, false><<<grid, NTH, 0, s>>>(a, b, c, len);
+    } else {
+        if (vec) matmul_simt_kernel<false, true><<<grid, NTH, 0, s>>>(a, b, c, len);
+        else matmul_simt_kernel<false, false><<<grid, NTH, 0, s>>>(a, b, c, len);
+    }
+    return launched("matmul_simt_kernel");
+}
+
+}  // namespace accr

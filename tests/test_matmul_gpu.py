@@ -1,0 +1,91 @@
+"""accr_matmul_nest (Listing 1a) on the GPU against the serial oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1412_1127_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 7, 33, 64, 100, 128, 129, 200, 256, 257, 300, 513]
+U = 2.0 ** -24
+
+
+def gpu_mm(a, b, mode):
+    at, bt = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    ct = torch.full_like(at, float("nan"))
+    api.accr_matmul_nest(at, bt, ct, mode=mode, flags=api.ACCR_SYNC)
+    return ct.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_serial_mode_is_the_serial_program(n):
+    a = inputs.uniform_matrix(n, n, salt=n)
+    b = inputs.uniform_matrix(n, n, salt=n + 1)
+    assert np.array_equal(gpu_mm(a, b, "serial"), oracle.matmul_listing1(a, b))
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fma_mode_error_bound(n):
+    a = inputs.uniform_matrix(n, n, salt=2 * n)
+    b = inputs.uniform_matrix(n, n, salt=2 * n + 1)
+    c = gpu_mm(a, b, "simt").astype(np.float64)
+    t, s = oracle.matmul_truth(a, b)
+    assert np.all(np.abs(c - t) <= (n + 2) * U * s + 1e-30)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_bf16x3_error_bound(n):
+    a = inputs.uniform_matrix(n, n, salt=3 * n)
+    b = inputs.uniform_matrix(n, n, salt=3 * n + 1)
+    c = gpu_mm(a, b, "bf16x3").astype(np.float64)
+    assert not np.isnan(c).any()
+    t, s = oracle.matmul_truth(a, b)
+    err = np.max(np.abs(c - t) / np.maximum(s, 1e-30))
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("n", [1, 16, 64, 130, 256])
+def test_small_integers_exact_in_every_mode(n):
+    a = inputs.small_int_matrix(n, n, salt=n)
+    b = inputs.small_int_matrix(n, n, salt=n + 5)
+    exact = (a.astype(np.int64) @ b.astype(np.int64)).astype(np.float32)
+    for mode in ["serial", "simt", "bf16x3"]:
+        assert np.array_equal(gpu_mm(a, b, mode), exact), mode
+
+
+def test_identity():
+    n = 200
+    a = inputs.uniform_matrix(n, n, salt=9)
+    eye = np.eye(n, dtype=np.float32)
+    assert np.array_equal(gpu_mm(a, eye, "serial"), a)
+    assert np.array_equal(gpu_mm(a, eye, "simt"), a)
+    c = gpu_mm(a, eye, "bf16x3")
+    assert np.all(np.abs(c - a) <= 2.0 ** -16 * np.abs(a))
+
+
+def test_full_size_sampled():
+    """LEN = 4096, U(-1,1): sampled entries against the oracle."""
+    n = 4096
+    a = inputs.uniform_matrix(n, n, salt=41)
+    b = inputs.uniform_matrix(n, n, salt=42)
+    at, bt = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = {}
+    for mode in ["serial", "simt", "bf16x3"]:
+        ct = torch.empty_like(at)
+        api.accr_matmul_nest(at, bt, ct, mode=mode, flags=api.ACCR_SYNC)
+        out[mode] = ct.cpu().numpy()
+    g = np.random.default_rng(0)
+    for i, j in zip(g.integers(0, n, 48), g.integers(0, n, 48)):
+        assert out["serial"][i, j] == oracle.matmul_listing1_at(a, b, i, j)
+        t, s = oracle.matmul_truth_at(a, b, i, j)
+        assert abs(float(out["simt"][i, j]) - t) <= (n + 2) * U * s
+        assert abs(float(out["bf16x3"][i, j]) - t) <= 1e-4 * s
+
+
+def test_rejects_bad_arguments():
+    x = torch.zeros(4, 4, device="cuda")
+    with pytest.raises(api._native.AccrError):
+        api.accr_matmul_nest(x, x, x, mode=7)
+    assert api.lib().accr_matmul_nest(None, None, None, -1, 0, 0, None) == api._native.ACCR_EINVAL
