@@ -330,6 +330,8 @@ def run_scalar(args):
         extra["served"] = measure_served(dev, args.served_seconds, args.rate)
         torch.cuda.empty_cache()
         extra["matmul"] = measure_matmul(dev)
+        torch.cuda.empty_cache()
+        extra["rows"] = measure_rows(dev)
 
     if rank == 0:
         line = {
@@ -543,7 +545,6 @@ def measure_matmul(dev, length=4096, reps=5):
     serial-order) and BF16x3 tcgen05, TFLOP/s of 2*LEN^3 and the error of
     sampled entries against the double-accumulated product."""
     import torch
-    import oracle
     from paper_1412_1127_gb300 import api, inputs
     a = inputs.uniform_matrix(length, length, salt=41)
     b = inputs.uniform_matrix(length, length, salt=42)
@@ -554,7 +555,11 @@ def measure_matmul(dev, length=4096, reps=5):
     peaks, kind = measured_peaks()
     g = np.random.default_rng(0)
     idx = list(zip(g.integers(0, length, 32), g.integers(0, length, 32)))
-    truth = [oracle.matmul_truth_at(a, b, int(i), int(j)) for i, j in idx]
+    # reference for the error report: double-accumulated products of the sampled entries
+    truth = []
+    for i, j in idx:
+        p = at[int(i), :].double() * bt[:, int(j)].double()
+        truth.append((float(p.sum()), float(p.abs().sum())))
     out = {"workload": "Listing-1 nest, LEN=%d, float U(-1,1)" % length}
     for mode in ["simt", "serial", "bf16x3"]:
         for _ in range(2):
@@ -579,10 +584,47 @@ def measure_matmul(dev, length=4096, reps=5):
     return out
 
 
+def measure_rows(dev, rows=65536, cols=4096, steps=10, warmup=3):
+    """The row nest: row sum and row max of a rows x cols float U(-1,1)
+    matrix in one pass (two clauses), GB/s of the matrix read once."""
+    import torch
+    from paper_1412_1127_gb300 import api, inputs
+    A = inputs.uniform_matrix(rows, cols)
+    At = torch.from_numpy(A).to(dev)
+    s = torch.empty(rows, dtype=torch.float32, device=dev)
+    m = torch.empty(rows, dtype=torch.float32, device=dev)
+    cls = [api.clause("add", s), api.clause("max", m)]
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(warmup, 3)):
+        api.accr_rowreduce(At, cls, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        api.accr_rowreduce(At, cls, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nbytes = rows * cols * 4
+    peaks, kind = measured_peaks()
+    ok_max = bool(torch.equal(m, At.amax(dim=1)))
+    return {"workload": "row sum + row max (one pass), %d x %d float U(-1,1)" % (rows, cols),
+            "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+            "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]), 4),
+            "row_max_equals_torch_amax": ok_max}
+
+
+def run_rows(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_rows(torch.device("cuda", 0), args.rows_m, 4096, args.steps, args.warmup)), flush=True)
+    return 0
+
+
 def run_matmul(args):
     import torch
     torch.cuda.set_device(0)
-    print(json.dumps(measure_matmul(torch.device("cuda", 0))), flush=True)
+    print(json.dumps(measure_matmul(torch.device("cuda", 0), args.len)), flush=True)
     return 0
 
 
@@ -601,7 +643,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="accr", choices=["accr", "reference"])
-    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served", "matmul"])
+    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served", "matmul", "rows"])
+    ap.add_argument("--len", type=int, default=4096, help="matmul: LEN")
+    ap.add_argument("--rows-m", type=int, default=65536, help="rows: number of rows (4096 columns)")
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--rate", type=float, default=50000.0)
     ap.add_argument("--no-extra", action="store_true",
@@ -623,6 +667,8 @@ def main():
         return run_served(args)
     if args.workload == "matmul":
         return run_matmul(args)
+    if args.workload == "rows":
+        return run_rows(args)
     return run_scalar(args)
 
 
