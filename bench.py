@@ -77,10 +77,18 @@ def measured_peaks():
 
 
 def source_hash(files):
+    """Hash of the device code of the given sources: a .cu file counts from its
+    first __global__ kernel to the "// ---- host side" marker (host-only edits
+    do not change the kernel), a header counts whole."""
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+            txt = fh.read()
+        if f.endswith(".cu"):
+            a = txt.find(b"__global__")
+            b = txt.find(b"// ---- host side")
+            txt = txt[a:b] if a >= 0 and b > a else txt
+        h.update(txt)
     return h.hexdigest()[:16]
 
 
@@ -158,6 +166,37 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def init_ranks(world, backend):
+    """Join the process group of a torchrun launch (127.0.0.1 rendezvous)."""
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The largest `value` over all ranks (every rank gets it)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank processes its own independent copy of the workload)."""
+    return units_per_rank * world / seconds
+
+
 def make_scalar_inputs(n, rank=0):
     from paper_1412_1127_gb300 import inputs
     return {"i32": inputs.full_range_i32(n, salt=rank),
@@ -216,9 +255,7 @@ def run_scalar(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    init_ranks(world, "nccl" if torch.cuda.is_available() else "gloo")
     n = args.n
     host = make_scalar_inputs(n, rank)
     devin = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
@@ -239,11 +276,6 @@ def run_scalar(args):
             if ev is not None:
                 ev[i][1].record(stream)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -253,7 +285,7 @@ def run_scalar(args):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     l0 = api.accr_launch_count()
     start.record(stream)
@@ -262,18 +294,13 @@ def run_scalar(args):
     stop.record(stream)
     torch.cuda.synchronize()
     launches = api.accr_launch_count() - l0
-    barrier()
+    barrier(world)
     clk = clocks.stop()
-    ms = start.elapsed_time(stop)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(stop), world, dev)
     per_region_ms = [sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)) / args.steps
                      for i in range(R)]
     ms_step = ms / args.steps
-    value = bytes_step * world / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(bytes_step, world, ms_step * 1e-3) / 1e9
 
     # results of the last step, checked against the oracle on a cheap subset
     peaks, peak_kind = measured_peaks()

@@ -355,6 +355,24 @@ ACCR_API int accr_reduce_noalloc(const void *in, int64_t n, int32_t in_type,
                                  const accr_clause *clauses, int32_t nclauses,
                                  uint32_t flags, accr_stream_t stream);
 
+/* ---- failure detection support ------------------------------------------------ */
+
+#define ACCR_FAULT_ALLOC 1  /* device / pinned allocations report ACCR_ENOMEM */
+#define ACCR_FAULT_LAUNCH 2 /* kernel launches are skipped and report ACCR_ECUDA */
+#define ACCR_FAULT_ADMIT 3  /* accr_submit reports ACCR_EBUDGET */
+
+/* Host-side fault injection for tests: the next `count` operations of `kind`
+ * (in any thread) fail as described above, without touching the GPU; count 0
+ * clears the kind.  Faults are made on the host only. */
+ACCR_API int accr_fault_inject(int32_t kind, int64_t count);
+
+/* Self-test of the bounded waits used inside the tensor-core pipeline: one CTA
+ * waits on an mbarrier that nothing ever arrives on, gives up after `tries`
+ * polls, records the expiry in a status word and exits.  Returns
+ * ACCR_ETIMEDOUT (the expected outcome) after the kernel has finished; the
+ * context stays usable. */
+ACCR_API int accr_selftest_wait_timeout(uint32_t tries, accr_stream_t stream);
+
 /* Message of the last error raised on the calling thread ("" if none). */
 ACCR_API const char *accr_last_error(void);
 

@@ -42,6 +42,10 @@ class OracleLib:
         L.oracle_matmul_listing1_at.restype = ctypes.c_float
         L.oracle_matmul_truth_at.argtypes = [vp, vp, i64, i64, i64, vp]
         L.oracle_matmul_truth_at.restype = ctypes.c_double
+        L.oracle_nearest_k.argtypes = [vp, i64, ctypes.c_float, ctypes.c_float, i, vp, vp]
+        L.oracle_standardize.argtypes = [vp, i64, vp, vp]
+        L.oracle_grid_bfs.argtypes = [vp, i64, i64, i64, vp]
+        L.oracle_grid_bfs.restype = i64
         self.L = L
         self.path = path
 
@@ -139,6 +143,33 @@ class OracleLib:
         return c, s[0]
 
 
+    def nearest_k(self, pts, qx, qy, k):
+        """(idx[k], d2[k]): the k points nearest to (qx, qy) by squared distance,
+        ties by index; pts is an (n, 2) float32 array."""
+        pts = np.ascontiguousarray(pts, dtype=np.float32)
+        n = pts.shape[0]
+        idx = np.zeros(k, dtype=np.int64)
+        d2 = np.zeros(k, dtype=np.float32)
+        self.L.oracle_nearest_k(_ptr(pts), n, ctypes.c_float(qx), ctypes.c_float(qy), k, _ptr(idx), _ptr(d2))
+        return idx, d2
+
+    def standardize(self, x):
+        """(y, (mean, var)): y = (x - mean) / sqrt(var) as the serial program computes it."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros_like(x)
+        st = np.zeros(2, dtype=np.float64)
+        self.L.oracle_standardize(_ptr(x), x.size, _ptr(y), _ptr(st))
+        return y, (st[0], st[1])
+
+    def grid_bfs(self, open_cells, src):
+        """(dist, levels): BFS distances on the grid of open cells (uint8, 2-D)."""
+        g = np.ascontiguousarray(open_cells, dtype=np.uint8)
+        rows, cols = g.shape
+        dist = np.zeros((rows, cols), dtype=np.int32)
+        levels = self.L.oracle_grid_bfs(_ptr(g), rows, cols, int(src), _ptr(dist))
+        return dist, int(levels)
+
+
 def _type_of(a):
     for k, v in _NP.items():
         if a.dtype == np.dtype(v):
@@ -206,3 +237,15 @@ def matmul_listing1_at(a, b, i, j):
 
 def matmul_truth_at(a, b, i, j):
     return default().matmul_truth_at(a, b, i, j)
+
+
+def nearest_k(pts, qx, qy, k):
+    return default().nearest_k(pts, qx, qy, k)
+
+
+def standardize(x):
+    return default().standardize(x)
+
+
+def grid_bfs(open_cells, src):
+    return default().grid_bfs(open_cells, src)

@@ -10,6 +10,7 @@
 
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
 
 /* ------------------------------------------------------------------------- */
@@ -403,4 +404,96 @@ void oracle_matmul_truth(const float *a, const float *b, double *c64,
         for (j = 0; j < len; ++j)
             c64[i * len + j] = oracle_matmul_truth_at(
                 a, b, len, i, j, absab ? &absab[i * len + j] : NULL);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Application patterns (Sec. 4.2).                                          */
+/* ------------------------------------------------------------------------- */
+
+/* (d, i) order: by distance, ties by index. */
+static int pair_less(float da, int64_t ia, float db, int64_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+void oracle_nearest_k(const float *pts, int64_t n, float qx, float qy, int k,
+                      int64_t *idx, float *d2)
+{
+    int64_t i;
+    int j;
+    /* k selection passes: each takes the smallest pair above the previous */
+    float last_d = -INFINITY;
+    int64_t last_i = -1;
+    for (j = 0; j < k; ++j) {
+        float best_d = INFINITY;
+        int64_t best_i = -1;
+        for (i = 0; i < n; ++i) {
+            float dx = pts[2 * i] - qx;
+            float dy = pts[2 * i + 1] - qy;
+            float d = dx * dx + dy * dy;
+            if (pair_less(last_d, last_i, d, i) &&
+                (best_i < 0 || pair_less(d, i, best_d, best_i))) {
+                best_d = d;
+                best_i = i;
+            }
+        }
+        idx[j] = best_i;
+        d2[j] = best_i < 0 ? INFINITY : best_d;
+        if (best_i >= 0) {
+            last_d = best_d;
+            last_i = best_i;
+        } else {
+            last_d = INFINITY;
+            last_i = INT64_MAX;
+        }
+    }
+}
+
+void oracle_standardize(const float *x, int64_t n, float *y, double *stats)
+{
+    int64_t i;
+    double s = 0.0, s2 = 0.0, mean, var;
+    float mean_f, rstd_f;
+    for (i = 0; i < n; ++i) {
+        s += (double)x[i];
+        s2 += (double)x[i] * (double)x[i];
+    }
+    mean = n > 0 ? s / (double)n : 0.0;
+    var = n > 0 ? s2 / (double)n - mean * mean : 0.0;
+    stats[0] = mean;
+    stats[1] = var;
+    mean_f = (float)mean;
+    rstd_f = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.0f;
+    for (i = 0; i < n; ++i) y[i] = (x[i] - mean_f) * rstd_f;
+}
+
+int64_t oracle_grid_bfs(const uint8_t *open, int64_t rows, int64_t cols,
+                        int64_t src, int32_t *dist)
+{
+    int64_t total = rows * cols, head = 0, tail = 0, c, levels = 0;
+    int64_t *queue;
+    for (c = 0; c < total; ++c) dist[c] = -1;
+    if (src < 0 || src >= total || !open[src]) return 0;
+    queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)total);
+    if (!queue) return -1;
+    dist[src] = 0;
+    queue[tail++] = src;
+    while (head < tail) {
+        int64_t u = queue[head++], r = u / cols, q = u % cols, nb[4];
+        int m, cnt = 0;
+        if (r > 0) nb[cnt++] = u - cols;
+        if (r + 1 < rows) nb[cnt++] = u + cols;
+        if (q > 0) nb[cnt++] = u - 1;
+        if (q + 1 < cols) nb[cnt++] = u + 1;
+        for (m = 0; m < cnt; ++m) {
+            int64_t v = nb[m];
+            if (open[v] && dist[v] < 0) {
+                dist[v] = dist[u] + 1;
+                queue[tail++] = v;
+            }
+        }
+        if (dist[u] + 1 > levels) levels = dist[u] + 1;
+    }
+    free(queue);
+    return levels;
 }

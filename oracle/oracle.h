@@ -98,4 +98,26 @@ float oracle_matmul_listing1_at(const float *a, const float *b, int64_t len,
 double oracle_matmul_truth_at(const float *a, const float *b, int64_t len,
                               int64_t i, int64_t j, double *absab);
 
+/* ---- patterns of the paper's applications (Sec. 4.2) ----------------------- */
+
+/* Nearest Neighbor: squared distances d_i = (x_i-qx)^2 + (y_i-qy)^2 of the n
+ * points pts[2i], pts[2i+1] (float arithmetic, each operation rounded), and the
+ * k smallest by (d, i) in increasing order.  idx[j] = -1 and d2[j] = +inf for
+ * j >= n. */
+void oracle_nearest_k(const float *pts, int64_t n, float qx, float qy, int k,
+                      int64_t *idx, float *d2);
+
+/* SRAD's reduction region feeding its data-parallel region, restated as the
+ * standardisation of an array: mean = sum x / n, var = sum x^2 / n - mean^2
+ * (sums in double), and y_i = (x_i - mean_f) * rstd_f with mean_f = (float)
+ * mean and rstd_f = (float)(1 / sqrt(var)).  stats = {mean, var}. */
+void oracle_standardize(const float *x, int64_t n, float *y, double *stats);
+
+/* BFS on a rows x cols grid (4-neighbour moves between open cells, open[c] !=
+ * 0), from the source cell: dist[c] = number of moves, -1 if unreachable
+ * (or the cell is closed).  Returns the number of levels (largest distance
+ * + 1), 0 if the source is closed. */
+int64_t oracle_grid_bfs(const uint8_t *open, int64_t rows, int64_t cols,
+                        int64_t src, int32_t *dist);
+
 #endif

@@ -303,6 +303,19 @@ def accr_matmul_nest(a, b, c, mode="simt", flags=0, stream=None):
                                         c.data_ptr() if n else None, n, m, flags, _stream(stream)))
 
 
+ACCR_FAULT_ALLOC, ACCR_FAULT_LAUNCH, ACCR_FAULT_ADMIT = 1, 2, 3
+
+
+def accr_fault_inject(kind, count):
+    """Host-side fault injection for tests (see include/accr.h)."""
+    return check(lib().accr_fault_inject(int(kind), int(count)))
+
+
+def accr_selftest_wait_timeout(tries=1000, stream=None):
+    """Runs the bounded-wait self-test; returns its status code (ACCR_ETIMEDOUT expected)."""
+    return int(lib().accr_selftest_wait_timeout(int(tries), _stream(stream)))
+
+
 def accr_last_error():
     return lib().accr_last_error().decode()
 

@@ -541,6 +541,8 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
     StreamBufs *B = bufs_for(stream);
     std::lock_guard<std::mutex> lk(B->mu);
     // device plan + partials
+    if ((B->dev_bytes < P.total_bytes || B->ncounters < R + 4) && fault_take(ACCR_FAULT_ALLOC))
+        return set_error(ACCR_ENOMEM, "batch: injected allocation failure");
     if (B->dev_bytes < P.total_bytes || B->ncounters < R + 4) {
         int rc = cuda_check(cudaStreamSynchronize(s), "batch: grow sync");
         if (rc != ACCR_OK) return rc;
@@ -597,6 +599,7 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
     rc = cuda_check(cudaEventRecord(B->stage_done[i], s), "batch: event record");
     if (rc != ACCR_OK) return rc;
     BatchArgs a = args_for(P, B->dev, B->counters);
+    if ((rc = launch_guard("batch_kernel")) != ACCR_OK) return rc;
     batch_kernel<<<batch_grid(P), BB, 0, s>>>(a);
     rc = launched("batch_kernel");
     if (rc != ACCR_OK) return rc;
@@ -730,7 +733,9 @@ extern "C" ACCR_API int accr_batch_launch(accr_batch *b, accr_stream_t stream) {
     clear_error();
     if (!b) return set_error(ACCR_EINVAL, "accr_batch_launch: batch is NULL");
     if (!b->exec) return ACCR_OK;  // empty batch
-    int rc = cuda_check(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "accr_batch_launch");
+    int rc = launch_guard("accr_batch_launch");
+    if (rc != ACCR_OK) return rc;
+    rc = cuda_check(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "accr_batch_launch");
     if (rc != ACCR_OK) return rc;
     rc = launched("batch_kernel (graph)");
     if (rc != ACCR_OK) return rc;

@@ -18,6 +18,12 @@ int cuda_check(cudaError_t e, const char *where);
 int launched(const char *what, int kernels = 1);
 void clear_error();
 
+// ---- host-side fault injection (tests) --------------------------------------
+// True if an injected fault of `kind` (ACCR_FAULT_*) fires now (and uses it up).
+bool fault_take(int kind);
+// Returns ACCR_ECUDA (message set) if an injected launch fault fires.
+int launch_guard(const char *what);
+
 // ---- device ---------------------------------------------------------------
 struct DeviceInfo {
     int id;

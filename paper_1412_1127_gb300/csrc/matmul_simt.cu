@@ -138,6 +138,8 @@ int matmul_simt(const float *a, const float *b, float *c, int64_t len, bool seri
     if (tiles > 65535) return set_error(ACCR_EINVAL, "accr_matmul_nest: len too large for the SIMT grid");
     dim3 grid((unsigned)tiles, (unsigned)tiles);
     // 16-byte vector access needs 16-byte aligned rows
+    int rc = launch_guard("matmul_simt_kernel");
+    if (rc != ACCR_OK) return rc;
     const bool vec = (len % 4 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0) && ((uintptr_t)c % 16 == 0);
     if (serial) {
         if (vec) matmul_simt_kernel<true, true><<<grid, NTH, 0, s>>>(a, b, c, len);

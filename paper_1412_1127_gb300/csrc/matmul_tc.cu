@@ -239,6 +239,29 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// Self-test of the bounded wait: nothing ever arrives on this barrier.
+__global__ void wait_selftest_kernel(uint32_t tries, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        for (uint32_t i = 0; i < tries && !ok; ++i) {
+            uint32_t r;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(r)
+                : "r"(smem_u32(&bar)), "r"(0u)
+                : "memory");
+            ok = r != 0;
+        }
+        if (!ok) atomicExch(err, 5);
+    }
+}
+
 // hi = bf16(x), lo = bf16(x - hi); a row-major M x K -> [M][Kp] (zero padded)
 __global__ void split_rows_kernel(const float *__restrict__ a, int64_t M, int64_t K, int64_t Kp,
                                   __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
@@ -326,6 +349,8 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lk(g_split_mu);
         sb = &g_split[std::make_pair(dev, (uintptr_t)s)];
+        if (sb->bytes < need && fault_take(ACCR_FAULT_ALLOC))
+            return set_error(ACCR_ENOMEM, "accr_matmul_nest: injected allocation failure");
         if (sb->bytes < need) {
             if (sb->buf) {
                 cudaStreamSynchronize(s);
@@ -344,7 +369,9 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     int *err = (int *)base;
     __nv_bfloat16 *ah = (__nv_bfloat16 *)(base + 256), *al = (__nv_bfloat16 *)(base + 256 + abytes);
     __nv_bfloat16 *bh = (__nv_bfloat16 *)(base + 256 + 2 * abytes), *bl = (__nv_bfloat16 *)(base + 256 + 2 * abytes + bbytes);
-    int rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_matmul_nest: clear flag");
+    int rc = launch_guard("bf16x3_gemm_kernel");
+    if (rc != ACCR_OK) return rc;
+    rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_matmul_nest: clear flag");
     if (rc != ACCR_OK) return rc;
     const DeviceInfo &di = device_info();
     split_rows_kernel<<<di.sms * 8, 256, 0, s>>>(a, M, K, Kp, ah, al);
@@ -375,4 +402,26 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     return rc;
 }
 
+int selftest_wait_timeout(uint32_t tries, cudaStream_t s) {
+    Scratch *scr = scratch_for((accr_stream_t)s, 64);
+    if (!scr) return ACCR_ENOMEM;
+    int *err = (int *)scr->buf;
+    int rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "selftest: clear");
+    if (rc != ACCR_OK) return rc;
+    if ((rc = launch_guard("wait_selftest_kernel")) != ACCR_OK) return rc;
+    wait_selftest_kernel<<<1, 32, 0, s>>>(tries, err);
+    if ((rc = launched("wait_selftest_kernel")) != ACCR_OK) return rc;
+    int h = 0;
+    rc = cuda_check(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s), "selftest: flag");
+    if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "selftest: sync");
+    if (rc != ACCR_OK) return rc;
+    if (h == 5) return set_error(ACCR_ETIMEDOUT, "selftest: the bounded wait ran out after %u polls", tries);
+    return ACCR_OK;
+}
+
 }  // namespace accr
+
+extern "C" ACCR_API int accr_selftest_wait_timeout(uint32_t tries, accr_stream_t stream) {
+    accr::clear_error();
+    return accr::selftest_wait_timeout(tries, (cudaStream_t)stream);
+}

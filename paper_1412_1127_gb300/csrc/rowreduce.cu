@@ -117,6 +117,8 @@ static int row_grid(int64_t rows) {
 
 template <typename T, int NC>
 static int row_launch_t(RowArgs &a, cudaStream_t s) {
+    int rc = launch_guard("rowreduce_kernel");
+    if (rc != ACCR_OK) return rc;
     rowreduce_kernel<T, NC><<<row_grid<T, NC>(a.rows), WB, 0, s>>>(a);
     return launched("rowreduce_kernel");
 }

@@ -35,6 +35,22 @@ int cuda_check(cudaError_t e, const char *where) {
     return set_error(ACCR_ECUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+static std::atomic<int64_t> g_faults[4];
+
+bool fault_take(int kind) {
+    if (kind < 1 || kind > 3) return false;
+    int64_t v = g_faults[kind].load(std::memory_order_relaxed);
+    while (v > 0) {
+        if (g_faults[kind].compare_exchange_weak(v, v - 1)) return true;
+    }
+    return false;
+}
+
+int launch_guard(const char *what) {
+    if (fault_take(ACCR_FAULT_LAUNCH)) return set_error(ACCR_ECUDA, "%s: injected launch failure", what);
+    return ACCR_OK;
+}
+
 int launched(const char *what, int kernels) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(e, what);
@@ -85,6 +101,10 @@ Scratch *scratch_for(accr_stream_t stream, size_t bytes) {
     std::lock_guard<std::mutex> lk(g_scr_mu);
     ScratchEntry *e = entry_for(stream);
     if (e->s.counters && e->s.bytes >= bytes) return &e->s;
+    if (fault_take(ACCR_FAULT_ALLOC)) {
+        set_error(ACCR_ENOMEM, "scratch: injected allocation failure");
+        return nullptr;
+    }
     // first use, or growth: the old buffer may still be read by work queued on
     // this stream, so drain the stream before releasing it
     if (e->s.counters) {
@@ -116,6 +136,10 @@ void *host_staging_for(accr_stream_t stream, size_t bytes) {
     std::lock_guard<std::mutex> lk(g_scr_mu);
     ScratchEntry *e = entry_for(stream);
     if (e->host && e->host_bytes >= bytes) return e->host;
+    if (fault_take(ACCR_FAULT_ALLOC)) {
+        set_error(ACCR_ENOMEM, "host staging: injected allocation failure");
+        return nullptr;
+    }
     if (e->host) {
         cudaStreamSynchronize((cudaStream_t)stream);
         cudaFreeHost(e->host);
@@ -141,6 +165,13 @@ extern "C" ACCR_API uint64_t accr_launch_count(void) {
 }
 
 extern "C" ACCR_API int32_t accr_version(void) { return ACCR_VERSION; }
+
+extern "C" ACCR_API int accr_fault_inject(int32_t kind, int64_t count) {
+    accr::clear_error();
+    if (kind < 1 || kind > 3 || count < 0) return accr::set_error(ACCR_EINVAL, "accr_fault_inject: bad kind or count");
+    accr::g_faults[kind].store(count);
+    return ACCR_OK;
+}
 
 // ---- clause lowering -----------------------------------------------------------
 #include "fold.cuh"

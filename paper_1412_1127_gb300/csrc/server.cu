@@ -232,6 +232,7 @@ extern "C" ACCR_API int accr_submit(accr_server *S, const accr_region *region, u
     Req q;
     q.region = *region;
     q.bytes = region->n * (int64_t)type_bytes(region->in_type);
+    if (fault_take(ACCR_FAULT_ADMIT)) return set_error(ACCR_EBUDGET, "accr_submit: injected admission rejection");
     if ((uint64_t)q.bytes > S->budget)
         return set_error(ACCR_EBUDGET, "accr_submit: region of %lld bytes exceeds the budget of %llu",
                          (long long)q.bytes, (unsigned long long)S->budget);

@@ -360,4 +360,74 @@ def pin_matmul_identity_and_transpose(orc):
     assert t == c64[5, 6] and ts == s[5, 6]
 
 
+# --------------------------------------------------------------------------
+# application patterns (Sec. 4.2): Nearest Neighbor, SRAD, BFS
+# --------------------------------------------------------------------------
+def _np_nearest(pts, qx, qy, k):
+    d = (pts[:, 0] - np.float32(qx)) * (pts[:, 0] - np.float32(qx)) + \
+        (pts[:, 1] - np.float32(qy)) * (pts[:, 1] - np.float32(qy))
+    order = np.lexsort((np.arange(len(d)), d))[:k]
+    return order, d[order]
+
+
+def pin_nearest_k(orc):
+    g = np.random.default_rng(31)
+    for n, k in [(1, 1), (5, 5), (7, 3), (1000, 5), (4097, 8), (3, 5), (0, 2)]:
+        pts = g.random((n, 2), dtype=np.float32) * 10
+        qx, qy = 3.25, 7.5
+        idx, d2 = orc.nearest_k(pts, qx, qy, k)
+        want_i, want_d = _np_nearest(pts, qx, qy, k)
+        m = min(n, k)
+        assert np.array_equal(idx[:m], want_i) and np.array_equal(d2[:m], want_d), (n, k)
+        assert np.all(idx[m:] == -1) and np.all(np.isinf(d2[m:]))
+    # ties: duplicate points are ordered by index
+    pts = np.array([[1, 1], [0, 0], [1, 1], [2, 2], [0, 0]], dtype=np.float32)
+    idx, d2 = orc.nearest_k(pts, 0.0, 0.0, 4)
+    assert idx.tolist() == [1, 4, 0, 2]
+
+
+def pin_standardize(orc):
+    g = np.random.default_rng(37)
+    x = (g.standard_normal(100001) * 3 + 5).astype(np.float32)
+    y, (mean, var) = orc.standardize(x)
+    xd = x.astype(np.float64)
+    assert abs(mean - xd.mean()) <= 1e-12 * abs(xd.mean())
+    assert abs(var - xd.var()) <= 1e-9 * xd.var()
+    assert abs(float(y.astype(np.float64).mean())) < 1e-5
+    assert abs(float(y.astype(np.float64).var()) - 1.0) < 1e-5
+    # affine invariance (positive scale) up to float rounding
+    y2, _ = orc.standardize((x * 2 + 1).astype(np.float32))
+    assert np.max(np.abs(y2 - y)) < 1e-5
+    c = np.full(10, 4.0, dtype=np.float32)
+    yc, (mc, vc) = orc.standardize(c)
+    assert mc == 4.0 and vc == 0.0 and np.all(yc == 0)
+
+
+def pin_grid_bfs(orc):
+    rows, cols = 13, 17
+    open_all = np.ones((rows, cols), dtype=np.uint8)
+    src = 5 * cols + 3
+    dist, levels = orc.grid_bfs(open_all, src)
+    rr, cc = np.indices((rows, cols))
+    assert np.array_equal(dist, np.abs(rr - 5) + np.abs(cc - 3))          # Manhattan distance
+    assert levels == int(dist.max()) + 1
+    import networkx as nx
+    g = np.random.default_rng(41)
+    for p_open in [0.9, 0.65]:
+        grid = (g.random((rows, cols)) < p_open).astype(np.uint8)
+        grid.flat[src] = 1
+        G = nx.grid_2d_graph(rows, cols)
+        G.remove_nodes_from([(r, c) for r in range(rows) for c in range(cols) if not grid[r, c]])
+        sp = nx.single_source_shortest_path_length(G, (5, 3))
+        want = np.full((rows, cols), -1, dtype=np.int32)
+        for (r, c), d in sp.items():
+            want[r, c] = d
+        dist, levels = orc.grid_bfs(grid, src)
+        assert np.array_equal(dist, want)
+    closed = open_all.copy()
+    closed.flat[src] = 0
+    dist, levels = orc.grid_bfs(closed, src)
+    assert levels == 0 and np.all(dist == -1)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

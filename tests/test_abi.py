@@ -87,3 +87,20 @@ def test_rowreduce_rejects_bad_arguments_on_host(L):
     assert L.accr_rowreduce(None, -1, 8, 8, 0, _clause(0, 0), 1, 0, None) == _native.ACCR_EINVAL
     assert L.accr_rowreduce(None, 4, 8, 8, 2, _clause(5, 2), 1, 0, None) == _native.ACCR_ETYPE
     assert L.accr_rowreduce(None, 4, 8, 8, 0, _clause(0, 0), 1, 0x4, None) == _native.ACCR_EINVAL
+
+
+def test_fault_inject_rejects_bad_kind(L):
+    assert L.accr_fault_inject(0, 1) == _native.ACCR_EINVAL
+    assert L.accr_fault_inject(4, 1) == _native.ACCR_EINVAL
+    assert L.accr_fault_inject(1, -1) == _native.ACCR_EINVAL
+    assert L.accr_fault_inject(2, 0) == _native.ACCR_OK
+
+
+def test_submit_and_server_reject_bad_arguments_on_host(L):
+    h = ctypes.c_void_p()
+    assert L.accr_server_create(0, 1, 1, ctypes.byref(h)) == _native.ACCR_EINVAL
+    assert L.accr_server_create(1 << 20, 0, 1, ctypes.byref(h)) == _native.ACCR_EINVAL
+    assert L.accr_submit(None, None, None) == _native.ACCR_EINVAL
+    assert L.accr_batch_create(None, 0, 0, None) == _native.ACCR_EINVAL
+    assert L.accr_batch_tiling(17, 0, None, None) == _native.ACCR_EINVAL
+    assert L.accr_matmul_nest(None, None, None, 4, 9, 0, None) == _native.ACCR_EINVAL

@@ -37,6 +37,11 @@ MUTANTS = [
     ("row_stride", "(size_t)(r * ld) * (size_t)ib", "(size_t)(r * cols) * (size_t)ib"),
     ("segment_bound", "int64_t lo = offsets[s], hi = offsets[s + 1];",
      "int64_t lo = offsets[s], hi = offsets[s + 1] - (offsets[s + 1] > offsets[s]);"),
+    ("nearest_tie_order", "return da < db || (da == db && ia < ib);", "return da < db || (da == db && ia > ib);"),
+    ("nearest_fma_like", "float d = dx * dx + dy * dy;", "float d = (float)((double)dx * dx + (double)dy * dy);"),
+    ("variance_sign", "var = n > 0 ? s2 / (double)n - mean * mean : 0.0;", "var = n > 0 ? s2 / (double)n + mean * mean : 0.0;"),
+    ("bfs_no_left_move", "if (q > 0) nb[cnt++] = u - 1;", ""),
+    ("bfs_ignores_walls", "if (open[v] && dist[v] < 0) {", "if (dist[v] < 0) {"),
     ("truth_abs_drops_sign", "la_add(&A, fabs(load_fp(x, in_type, i * stride)));",
      "la_add(&A, load_fp(x, in_type, i * stride));"),
 ]
