@@ -359,6 +359,8 @@ def run_scalar(args):
         extra["matmul"] = measure_matmul(dev)
         torch.cuda.empty_cache()
         extra["rows"] = measure_rows(dev)
+        torch.cuda.empty_cache()
+        extra["patterns"] = measure_patterns(dev)
 
     if rank == 0:
         line = {
@@ -648,6 +650,102 @@ def run_rows(args):
     return 0
 
 
+def measure_patterns(dev, reps=10):
+    """The survey's next rows: the paper's two-level host merge against the
+    single-pass merge (f1), the SRAD pattern fused and unfused (f2), the BFS
+    convergence flag in its three forms (f3), and k-nearest (f4)."""
+    import torch
+    from paper_1412_1127_gb300 import api, inputs
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def wall(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(k):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)) * 1e3
+
+    # f1: result of one region available on the host
+    f1 = {}
+    for lg in (20, 24, 28):
+        x = torch.from_numpy(inputs.full_range_i32(1 << lg, salt=lg)).to(dev)
+        sd = torch.empty(1, dtype=torch.int64, device=dev)
+        sh = torch.empty(1, dtype=torch.int64).pin_memory()
+
+        def single():
+            # the last CTA writes the variable straight into pinned host memory
+            api.accr_reduce(x, [api.clause("add", sh)], flags=api.ACCR_SYNC, stream=stream)
+
+        def two_level():
+            api.accr_reduce(x, [api.clause("add", sh)], flags=api.ACCR_TWO_LEVEL_HOST, stream=stream)
+
+        a, b = wall(single, reps), wall(two_level, reps)
+        f1["2^%d" % lg] = {"single_pass_ms": round(a, 4), "two_level_host_ms": round(b, 4)}
+        del x
+    out["f1_two_level_vs_single_pass"] = f1
+
+    # f2: SRAD pattern (statistics, then the standardised array)
+    f2 = {}
+    for lg in (22, 28):
+        n = 1 << lg
+        x = torch.from_numpy(inputs.normal(n, np.float32, salt=lg)).to(dev)
+        y = torch.empty_like(x)
+        st = torch.empty(2, dtype=torch.float64, device=dev)
+        r = {}
+        for form, fl in [("fused", 0), ("unfused", api.ACCR_UNFUSED), ("two_level_host", api.ACCR_TWO_LEVEL_HOST)]:
+            ms = wall(lambda: (api.accr_standardize(x, y, st, flags=fl, stream=stream), stream.synchronize()), reps)
+            r[form] = {"ms": round(ms, 4), "gbs_3_passes": round(12.0 * n / (ms * 1e-3) / 1e9, 1)}
+        f2["n=2^%d" % lg] = r
+        del x, y
+    out["f2_srad_pattern"] = f2
+
+    # f3: BFS convergence loop on a 1024 x 1024 grid, 62 % open
+    g = inputs.rng(23, 1)
+    grid = (g.random((1024, 1024)) < 0.62).astype(np.uint8)
+    src = 512 * 1024 + 512
+    grid.flat[src] = 1
+    gt = torch.from_numpy(grid).to(dev)
+    dist = torch.empty((1024, 1024), dtype=torch.int32, device=dev)
+    f3 = {}
+    for mode in ["reduce", "guarded", "persistent"]:
+        lv = [0]
+
+        def run():
+            lv[0] = api.accr_grid_bfs(gt, src, dist, mode=mode, stream=stream)
+        ms = wall(run, 3)
+        f3[mode] = {"ms": round(ms, 3), "levels": lv[0], "us_per_level": round(ms * 1e3 / max(lv[0], 1), 2)}
+    out["f3_bfs_convergence"] = f3
+
+    # f4: k = 5 nearest of 2^26 points
+    n = 1 << 26
+    pts = torch.from_numpy((inputs.rng(21, 5).random((n, 2), dtype=np.float32) * 100)).to(dev)
+    idx = torch.empty(5, dtype=torch.int64, device=dev)
+    d2 = torch.empty(5, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        api.accr_nearest_k(pts, 41.5, 58.25, 5, idx, d2, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        api.accr_nearest_k(pts, 41.5, 58.25, 5, idx, d2, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out["f4_nearest_k5"] = {"n": n, "ms": round(ms, 4), "gbs": round(8.0 * n / (ms * 1e-3) / 1e9, 1)}
+    return out
+
+
+def run_patterns(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_patterns(torch.device("cuda", 0))), flush=True)
+    return 0
+
+
 def run_matmul(args):
     import torch
     torch.cuda.set_device(0)
@@ -670,7 +768,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="accr", choices=["accr", "reference"])
-    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served", "matmul", "rows"])
+    ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served", "matmul", "rows", "patterns"])
     ap.add_argument("--len", type=int, default=4096, help="matmul: LEN")
     ap.add_argument("--rows-m", type=int, default=65536, help="rows: number of rows (4096 columns)")
     ap.add_argument("--served-seconds", type=float, default=2.0)
@@ -696,6 +794,8 @@ def main():
         return run_matmul(args)
     if args.workload == "rows":
         return run_rows(args)
+    if args.workload == "patterns":
+        return run_patterns(args)
     return run_scalar(args)
 
 

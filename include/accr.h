@@ -92,6 +92,7 @@ typedef enum {
                                    pointer and the call is synchronous */
 
 #define ACCR_PLAIN 0x8u          /* accr_batch_reduce: one launch per region */
+#define ACCR_UNFUSED 0x10u       /* accr_standardize: two launches */
 
 #define ACCR_MAX_CLAUSES 4
 
@@ -105,7 +106,9 @@ typedef struct {
     const void *init; /* HOST pointer to the variable's value before the
                          region (read during the call), or NULL = identity */
     void *out;        /* DEVICE pointer receiving the variable's value after
-                         the region (host pointer under ACCR_TWO_LEVEL_HOST) */
+                         the region, or pinned (page-locked) host memory, which
+                         the last CTA then writes directly; ordinary host
+                         memory under ACCR_TWO_LEVEL_HOST */
 } accr_clause;
 
 /*
@@ -261,6 +264,57 @@ ACCR_API int accr_batch_tiling(int64_t small_bytes, int64_t tile_bytes,
                                int64_t *old_small, int64_t *old_tile);
 #define ACCR_SMALL_BYTES 65536
 #define ACCR_TILE_BYTES 2097152
+
+/* ---- patterns of the paper's applications (Sec. 4.2) -------------------------- */
+
+/*
+ * accr_nearest_k -- Nearest Neighbor: the k (1..16) points nearest to
+ * (qx, qy).  d_i = (x_i - qx)^2 + (y_i - qy)^2 in float, every operation
+ * rounded (no fused multiply-add); the k smallest by (d, i), ties by index,
+ * in increasing order -- a reduction whose operator keeps a sorted list.
+ *
+ *   pts       DEVICE, n points as float pairs (x0, y0, x1, y1, ...), 8-byte aligned
+ *   idx_out   DEVICE int64[k]; d2_out DEVICE float[k] (-1 / +inf past n)
+ *   flags     ACCR_SYNC
+ */
+ACCR_API int accr_nearest_k(const float *pts, int64_t n, float qx, float qy,
+                            int32_t k, int64_t *idx_out, float *d2_out,
+                            uint32_t flags, accr_stream_t stream);
+
+/*
+ * accr_standardize -- SRAD's reduction region feeding its data-parallel
+ * region: mean = sum x / n and var = sum x^2 / n - mean^2 (compensated float
+ * sums, merged in double), then y_i = (x_i - (float)mean) * (float)(1/sqrt(var))
+ * (y may alias x).  stats receives {mean, var} (DEVICE double[2]).
+ *
+ * Default: one cooperative launch -- the last CTA of the reduction publishes
+ * the statistics and every CTA waits for them (bounded) before the
+ * elementwise pass.  ACCR_UNFUSED: two launches, statistics kept on the
+ * device.  ACCR_TWO_LEVEL_HOST: the paper's form (partials merged on the
+ * host, then the elementwise launch; synchronous).
+ *   flags     ACCR_SYNC | ACCR_UNFUSED | ACCR_TWO_LEVEL_HOST
+ */
+ACCR_API int accr_standardize(const float *x, int64_t n, float *y,
+                              double *stats, uint32_t flags,
+                              accr_stream_t stream);
+
+#define ACCR_BFS_REDUCE 0     /* levels driven by the host; || reduction of the flag */
+#define ACCR_BFS_GUARDED 1    /* levels driven by the host; flag cleared, threads write only 1 */
+#define ACCR_BFS_PERSISTENT 2 /* all levels in one cooperative launch, grid barriers */
+
+/*
+ * accr_grid_bfs -- BFS's convergence loop: level-synchronous search on a
+ * rows x cols grid of cells (open[c] != 0 is passable, 4-neighbour moves) from
+ * cell `src`: dist[c] = number of moves, -1 if unreachable.  The loop stops
+ * when a level changes no cell; *levels (HOST) = largest distance + 1 (0 if
+ * the source is closed).  Synchronous.
+ *
+ *   open      DEVICE uint8[rows*cols]; dist DEVICE int32[rows*cols]
+ *   mode      ACCR_BFS_REDUCE | ACCR_BFS_GUARDED | ACCR_BFS_PERSISTENT
+ */
+ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t cols,
+                           int64_t src, int32_t *dist, int32_t mode,
+                           int64_t *levels, accr_stream_t stream);
 
 /* ---- served request loop ---------------------------------------------------- */
 

@@ -70,6 +70,9 @@ SIGNATURES = {
     "accr_server_replay": (ctypes.c_int, [_vp, ctypes.POINTER(Region), ctypes.POINTER(ctypes.c_double), _i64,
                                           _u32, _vp, ctypes.POINTER(Result)]),
     "accr_matmul_nest": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i32, _u32, _vp]),
+    "accr_nearest_k": (ctypes.c_int, [_vp, _i64, ctypes.c_float, ctypes.c_float, _i32, _vp, _vp, _u32, _vp]),
+    "accr_standardize": (ctypes.c_int, [_vp, _i64, _vp, _vp, _u32, _vp]),
+    "accr_grid_bfs": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i32, ctypes.POINTER(_i64), _vp]),
     "accr_reduce_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_fault_inject": (ctypes.c_int, [_i32, _i64]),
     "accr_selftest_wait_timeout": (ctypes.c_int, [_u32, _vp]),

@@ -13,7 +13,7 @@ from ._native import Clause, check, lib
 
 ACCR_I32, ACCR_I64, ACCR_F32, ACCR_F64 = 0, 1, 2, 3
 ACCR_ADD, ACCR_MUL, ACCR_MAX, ACCR_MIN, ACCR_BAND, ACCR_BOR, ACCR_BXOR, ACCR_LAND, ACCR_LOR = range(9)
-ACCR_COMPENSATED, ACCR_SYNC, ACCR_TWO_LEVEL_HOST, ACCR_PLAIN = 0x1, 0x2, 0x4, 0x8
+ACCR_COMPENSATED, ACCR_SYNC, ACCR_TWO_LEVEL_HOST, ACCR_PLAIN, ACCR_UNFUSED = 0x1, 0x2, 0x4, 0x8, 0x10
 ACCR_MAX_CLAUSES = 4
 ACCR_SMALL_BYTES = 65536   # default split of batched regions (include/accr.h)
 ACCR_TILE_BYTES = 2097152
@@ -85,7 +85,8 @@ def accr_reduce(x, clauses, flags=0, stream=None, n=None):
     assert 0 <= n <= x.numel()
     two_level = bool(flags & ACCR_TWO_LEVEL_HOST)
     for c in clauses:
-        assert c.out.numel() >= 1 and c.out.is_cuda != two_level
+        assert c.out.numel() >= 1
+        assert (not c.out.is_cuda) if two_level else (c.out.is_cuda or c.out.is_pinned())
     arr, keep = _clauses(clauses)
     return check(lib().accr_reduce(x.data_ptr() if x.numel() else None, n, type_of(x.dtype), arr,
                                    len(clauses), flags, _stream(stream)))
@@ -237,8 +238,10 @@ class Server:
         self._keep[t.value] = (x, keep)
         return t.value
 
-    def poll(self, ticket, timeout_us=-1):
-        """(status, [values...]) of a ticket; values decoded by variable type."""
+    def poll(self, ticket, timeout_us=60_000_000):
+        """(status, [values...], result) of a ticket, waiting at most timeout_us
+        (-1: no limit); returns (ACCR_EAGAIN / ACCR_ETIMEDOUT, None, ...) if it
+        is not ready."""
         r = _native.Result()
         rc = lib().accr_poll(self.handle, ticket, ctypes.byref(r), int(timeout_us))
         if rc == _native.ACCR_EAGAIN or rc == _native.ACCR_ETIMEDOUT:
@@ -314,6 +317,44 @@ def accr_fault_inject(kind, count):
 def accr_selftest_wait_timeout(tries=1000, stream=None):
     """Runs the bounded-wait self-test; returns its status code (ACCR_ETIMEDOUT expected)."""
     return int(lib().accr_selftest_wait_timeout(int(tries), _stream(stream)))
+
+
+def accr_nearest_k(pts, qx, qy, k, idx_out, d2_out, flags=0, stream=None):
+    """Nearest Neighbor: the k points of pts (CUDA float tensor (n, 2)) nearest
+    to (qx, qy); indices into idx_out (int64[k]) and squared distances into
+    d2_out (float[k])."""
+    assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.dim() == 2
+    assert idx_out.dtype == torch.int64 and d2_out.dtype == torch.float32
+    assert idx_out.numel() >= k and d2_out.numel() >= k
+    return check(lib().accr_nearest_k(pts.data_ptr() if pts.numel() else None, pts.shape[0], float(qx), float(qy),
+                                      int(k), idx_out.data_ptr(), d2_out.data_ptr(), flags, _stream(stream)))
+
+
+def accr_standardize(x, y, stats, flags=0, stream=None):
+    """SRAD pattern: stats <- (mean, var) of x; y <- (x - mean) / sqrt(var)."""
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+    assert y.is_cuda and y.dtype == torch.float32 and y.numel() == x.numel()
+    assert stats.is_cuda and stats.dtype == torch.float64 and stats.numel() >= 2
+    return check(lib().accr_standardize(x.data_ptr() if x.numel() else None, x.numel(),
+                                        y.data_ptr() if y.numel() else None, stats.data_ptr(), flags,
+                                        _stream(stream)))
+
+
+ACCR_BFS_REDUCE, ACCR_BFS_GUARDED, ACCR_BFS_PERSISTENT = 0, 1, 2
+BFS_MODES = {"reduce": 0, "guarded": 1, "persistent": 2}
+
+
+def accr_grid_bfs(open_cells, src, dist, mode="reduce", stream=None):
+    """BFS pattern: distances on a grid of open cells (CUDA uint8 (rows, cols));
+    returns the number of levels."""
+    assert open_cells.is_cuda and open_cells.dtype == torch.uint8 and open_cells.is_contiguous()
+    assert dist.is_cuda and dist.dtype == torch.int32 and dist.shape == open_cells.shape
+    rows, cols = open_cells.shape
+    lv = ctypes.c_int64()
+    m = BFS_MODES[mode] if isinstance(mode, str) else int(mode)
+    check(lib().accr_grid_bfs(open_cells.data_ptr(), rows, cols, int(src), dist.data_ptr(), m,
+                              ctypes.byref(lv), _stream(stream)))
+    return lv.value
 
 
 def accr_last_error():

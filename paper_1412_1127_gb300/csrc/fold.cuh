@@ -279,9 +279,26 @@ __device__ __forceinline__ void fold_vec(int w, Acc &A, const uint4 *v) {
         constexpr bool F32 = std::is_same<T, float>::value;
         switch (w) {
         case W_ADDF: {
-            T a = F32 ? (T)u2f((uint32_t)A.a) : (T)u2d(A.a);
-            for_each_elem<T, NV>(v, [&](T x) { a = a + x; });
-            if constexpr (F32) A.a = f2u((float)a); else A.a = d2u((double)a);
+            if constexpr (F32) {
+                float a = u2f((uint32_t)A.a);
+                for_each_elem<T, NV>(v, [&](T x) { a = a + x; });
+                A.a = f2u(a);
+            } else {
+                // double: the chunk is summed as a pairwise tree, then added
+                // (as many adds as a chain, but a dependency depth of log2 +1,
+                // which keeps the FP64 pipe fed)
+                double e[2 * NV];
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    e[2 * i] = u2d(word64(v[i], 0));
+                    e[2 * i + 1] = u2d(word64(v[i], 1));
+                }
+#pragma unroll
+                for (int w = 1; w < 2 * NV; w *= 2)
+#pragma unroll
+                    for (int i = 0; i + w < 2 * NV; i += 2 * w) e[i] = __dadd_rn(e[i], e[i + w]);
+                A.a = d2u(__dadd_rn(u2d(A.a), e[0]));
+            }
         } break;
         case W_ADDF_COMP: {
             if constexpr (F32) {

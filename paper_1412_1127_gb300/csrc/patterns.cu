@@ -1,0 +1,887 @@
+// patterns.cu -- three region patterns from the paper's application study
+// (IPMACC Sec. 4.2), on the same single-pass reduction machinery:
+//
+//  * Nearest Neighbor: distances to a query point and the k smallest -- a
+//    reduction whose operator keeps a sorted list of k (distance, index)
+//    pairs.  Each thread keeps its list in registers, a warp merges its 32
+//    lists by popping the smallest head k times (butterfly argmin), the CTA
+//    merges its warps' lists, and the last CTA to finish merges the CTA lists.
+//
+//  * SRAD: a reduction region whose result feeds a data-parallel region.  The
+//    paper's OpenACC code merges the block partials on the CPU and launches
+//    the next region; here one cooperative launch does both: the last CTA of
+//    the reduction publishes the statistics, every CTA waits for them at a
+//    bounded grid barrier and then runs the elementwise pass (for arrays that
+//    fit in L2 the second pass reads from L2).  Unfused and two-level host
+//    forms are kept for comparison.
+//
+//  * BFS: a level-synchronous loop that stops when no cell changed.  The
+//    OpenACC version reduces a global boolean with ||; the CUDA version
+//    initialises the flag and lets threads write only `true`.  Both forms run
+//    here with the host driving the levels, and a third keeps every level in
+//    one cooperative launch with a bounded grid barrier between levels.
+//
+// Every cross-CTA wait spins a bounded number of times; on expiry it records
+// a code in a status word and the host reports ACCR_ETIMEDOUT.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+#include "fold.cuh"
+
+namespace accr {
+
+constexpr uint32_t kSpinLimit = 20000000u;  // ~seconds of __nanosleep(64) polls
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier for a cooperative launch: generation counting, bounded spin.
+// bar[0] = arrivals, bar[1] = generation.  Returns false if the wait ran out.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &gen) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        const unsigned my = gen + 1;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            st_release(&bar[1], my);
+        } else {
+            uint32_t i = 0;
+            while (ld_acquire(&bar[1]) != my) {
+                if (++i > kSpinLimit) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+    }
+    gen += 1;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_ok = ok;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ============================================================================
+// Nearest Neighbor: k smallest squared distances
+// ============================================================================
+
+constexpr int NK_THREADS = 256;
+
+struct __align__(16) PairSlot {
+    int64_t i;
+    float d;
+    uint32_t pad;
+};
+
+__device__ __forceinline__ bool pless(float da, int64_t ia, float db, int64_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+template <int KT>
+__device__ __forceinline__ void list_init(float (&D)[KT], int64_t (&I)[KT]) {
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+        D[j] = INFINITY;
+        I[j] = INT64_MAX;
+    }
+}
+
+// Inserts (d, i) into the ascending list if it belongs to the KT smallest.
+template <int KT>
+__device__ __forceinline__ void list_insert(float (&D)[KT], int64_t (&I)[KT], float d, int64_t i) {
+    if (!pless(d, i, D[KT - 1], I[KT - 1])) return;
+    bool placed = false;
+#pragma unroll
+    for (int j = KT - 1; j > 0; --j) {
+        if (!placed) {
+            if (pless(d, i, D[j - 1], I[j - 1])) {
+                D[j] = D[j - 1];
+                I[j] = I[j - 1];
+            } else {
+                D[j] = d;
+                I[j] = i;
+                placed = true;
+            }
+        }
+    }
+    if (!placed) {
+        D[0] = d;
+        I[0] = i;
+    }
+}
+
+// Merges the 32 lanes' lists into the warp's KT smallest (every lane gets R).
+template <int KT>
+__device__ __forceinline__ void warp_topk(float (&D)[KT], int64_t (&I)[KT], float (&RD)[KT], int64_t (&RI)[KT]) {
+#pragma unroll
+    for (int r = 0; r < KT; ++r) {
+        float bd = D[0];
+        int64_t bi = I[0];
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, bd, m);
+            const int64_t oi = (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)bi, m);
+            if (pless(od, oi, bd, bi)) {
+                bd = od;
+                bi = oi;
+            }
+        }
+        RD[r] = bd;
+        RI[r] = bi;
+        if (D[0] == bd && I[0] == bi) {  // my head was taken: pop it
+#pragma unroll
+            for (int j = 0; j < KT - 1; ++j) {
+                D[j] = D[j + 1];
+                I[j] = I[j + 1];
+            }
+            D[KT - 1] = INFINITY;
+            I[KT - 1] = INT64_MAX;
+        }
+    }
+}
+
+__device__ __forceinline__ float sqdist(float x, float y, float qx, float qy) {
+    const float dx = __fsub_rn(x, qx), dy = __fsub_rn(y, qy);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));  // no fused multiply-add
+}
+
+// One list per warp in shared memory; every lane keeps the warp's current
+// k-th entry (the threshold) in registers.  A lane's candidate that beats the
+// threshold is found by a ballot; such candidates (rare once the list has
+// filled) go through the out-of-line slow path one at a time, lane 0 inserting
+// into the shared list.  The expected number of insertions per warp grows
+// only with the log of the points it scans.
+struct Thr {
+    float d;
+    int64_t i;
+};
+
+template <int KT>
+__device__ __noinline__ Thr warp_insert_slow(float *LD, int64_t *LI, float d, int64_t i, unsigned mask) {
+    const int lane = threadIdx.x & 31;
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float cd = __shfl_sync(0xffffffffu, d, src);
+        const int64_t ci = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
+        if (lane == 0 && pless(cd, ci, LD[KT - 1], LI[KT - 1])) {
+            int j = KT - 1;
+            while (j > 0 && pless(cd, ci, LD[j - 1], LI[j - 1])) {
+                LD[j] = LD[j - 1];
+                LI[j] = LI[j - 1];
+                --j;
+            }
+            LD[j] = cd;
+            LI[j] = ci;
+        }
+        __syncwarp();
+    }
+    Thr t;
+    t.d = LD[KT - 1];
+    t.i = LI[KT - 1];
+    __syncwarp();
+    return t;
+}
+
+template <int KT>
+__device__ __forceinline__ void warp_offer(float *LD, int64_t *LI, Thr &thr, float d, int64_t i) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pless(d, i, thr.d, thr.i));
+    if (mask) thr = warp_insert_slow<KT>(LD, LI, d, i, mask);
+}
+
+// Warp 0 merges the CTA's warp lists (shared memory) into the CTA's KT
+// smallest, held in D/I of every lane of warp 0.
+template <int KT, int NT>
+__device__ __forceinline__ void cta_merge_warp_lists(float (&D)[KT], int64_t (&I)[KT], float (*wld)[KT],
+                                                     int64_t (*wli)[KT]) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        if (lane < NT / 32) {
+#pragma unroll
+            for (int j = 0; j < KT; ++j) {
+                D[j] = wld[lane][j];
+                I[j] = wli[lane][j];
+            }
+        } else {
+            list_init<KT>(D, I);
+        }
+        float RD[KT];
+        int64_t RI[KT];
+        warp_topk<KT>(D, I, RD, RI);
+#pragma unroll
+        for (int j = 0; j < KT; ++j) {
+            D[j] = RD[j];
+            I[j] = RI[j];
+        }
+    }
+    __syncthreads();
+}
+
+template <int KT, int NT>
+__global__ void __launch_bounds__(NT) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
+                                                     int k, int64_t *idx_out, float *d_out, PairSlot *partials,
+                                                     unsigned *counter) {
+    __shared__ float wld[NT / 32][KT];
+    __shared__ int64_t wli[NT / 32][KT];
+    __shared__ int am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *LD = wld[warp];
+    int64_t *LI = wli[warp];
+    if (lane < KT) {
+        LD[lane] = INFINITY;
+        LI[lane] = INT64_MAX;
+    }
+    __syncwarp();
+    Thr thr;
+    thr.d = INFINITY;
+    thr.i = INT64_MAX;
+    // points are float2; the vector part starts at a 16-byte boundary
+    const int64_t head = (((uintptr_t)pts & 15) != 0 && n > 0) ? 1 : 0;
+    const float4 *v4 = (const float4 *)(pts + 2 * head);
+    const int64_t npairs = (n - head) / 2;
+    const int64_t nth = (int64_t)gridDim.x * NT;
+    if (blockIdx.x == 0 && warp == 0) {  // the unaligned first point and the odd last point
+        const int64_t last = head + 2 * npairs;
+        float d = INFINITY;
+        int64_t i = INT64_MAX;
+        if (lane == 0 && head) d = sqdist(pts[0], pts[1], qx, qy), i = 0;
+        if (lane == 1 && last < n) d = sqdist(pts[2 * last], pts[2 * last + 1], qx, qy), i = last;
+        warp_offer<KT>(LD, LI, thr, d, i);
+    }
+    // NU 16-byte loads (2 points each) in flight per lane per iteration; the
+    // trip count is uniform across each warp so that the ballots see 32 lanes
+    constexpr int NU = 4;
+    const int64_t vstep = nth * NU;
+    const int64_t base0 = (int64_t)blockIdx.x * (NT * NU) + warp * 32;
+    auto load = [&](int64_t vb, float4 (&q)[NU]) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int64_t vv = vb + lane + u * NT;
+            q[u] = vv < npairs ? __ldg(v4 + vv) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    float4 qn[NU];
+    load(base0, qn);  // software pipeline: the next vectors are in flight while these are offered
+    for (int64_t vb = base0; vb < npairs; vb += vstep) {
+        float4 q[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) q[u] = qn[u];
+        if (vb + vstep < npairs) load(vb + vstep, qn);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int64_t vv = vb + lane + u * NT;
+            const bool ok = vv < npairs;
+            const int64_t i0 = head + 2 * vv;
+            warp_offer<KT>(LD, LI, thr, ok ? sqdist(q[u].x, q[u].y, qx, qy) : INFINITY, ok ? i0 : INT64_MAX);
+            warp_offer<KT>(LD, LI, thr, ok ? sqdist(q[u].z, q[u].w, qx, qy) : INFINITY, ok ? i0 + 1 : INT64_MAX);
+        }
+    }
+    float D[KT];
+    int64_t I[KT];
+    cta_merge_warp_lists<KT, NT>(D, I, wld, wli);
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < KT; ++j) {
+            PairSlot p;
+            p.i = I[j];
+            p.d = D[j];
+            p.pad = 0;
+            partials[(int64_t)blockIdx.x * KT + j] = p;
+        }
+        __threadfence();
+        am_last = atomicAdd(counter, 1u) == (unsigned)G - 1u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    if (lane < KT) {
+        LD[lane] = INFINITY;
+        LI[lane] = INT64_MAX;
+    }
+    __syncwarp();
+    thr.d = INFINITY;
+    thr.i = INT64_MAX;
+    const int64_t nc = (int64_t)G * KT;
+    for (int64_t c0 = 0; c0 < nc; c0 += NT) {  // uniform trip count: whole warps take part in the ballots
+        const int64_t c = c0 + threadIdx.x;
+        float d = INFINITY;
+        int64_t i = INT64_MAX;
+        if (c < nc) {
+            const uint4 raw = __ldcg(reinterpret_cast<const uint4 *>(partials + c));
+            i = (int64_t)(((uint64_t)raw.y << 32) | raw.x);
+            d = __uint_as_float(raw.z);
+        }
+        warp_offer<KT>(LD, LI, thr, d, i);
+    }
+    cta_merge_warp_lists<KT, NT>(D, I, wld, wli);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < k; ++j) {
+            const bool real = I[j] != INT64_MAX;
+            idx_out[j] = real ? I[j] : -1;
+            d_out[j] = real ? D[j] : INFINITY;
+        }
+        *counter = 0u;
+    }
+}
+
+template <int KT>
+static int nearest_launch(const float *pts, int64_t n, float qx, float qy, int k, int64_t *idx, float *d,
+                          cudaStream_t s) {
+    constexpr int NT = NK_THREADS;
+    static int per_sm = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nearest_kernel<KT, NT>, NT, 0);
+        if (per_sm < 1) per_sm = 1;
+    });
+    const DeviceInfo &di = device_info();
+    int64_t want = (n / 2 + NT * 4 - 1) / (NT * 4);  // 4 vectors per thread
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
+    Scratch *scr = scratch_for((accr_stream_t)s, sizeof(PairSlot) * (size_t)grid * KT);
+    if (!scr) return ACCR_ENOMEM;
+    int rc = launch_guard("nearest_kernel");
+    if (rc != ACCR_OK) return rc;
+    nearest_kernel<KT, NT><<<grid, NT, 0, s>>>(pts, n, qx, qy, k, idx, d, (PairSlot *)scr->buf,
+                                                    scr->counters + 1);
+    return launched("nearest_kernel");
+}
+
+// ============================================================================
+// SRAD pattern: statistics of an array, then the standardised array
+// ============================================================================
+
+constexpr int SD_THREADS = 512;
+
+struct __align__(16) StatPartial {
+    float s1, c1, s2, c2;  // compensated sum of x and of x^2
+};
+
+struct StdShared {
+    double mean, var;
+    float mean_f, rstd_f;
+};
+
+__device__ __forceinline__ void stat_merge(float &s1, float &c1, float &s2, float &c2, float t1, float e1, float t2,
+                                           float e2) {
+    two_sum_merge(s1, c1, t1, e1);
+    two_sum_merge(s2, c2, t2, e2);
+}
+
+// CTA merge of the four running values; thread 0 ends with the totals.
+__device__ __forceinline__ void stat_cta(float &s1, float &c1, float &s2, float &c2, StatPartial *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const float t1 = __shfl_xor_sync(0xffffffffu, s1, m), e1 = __shfl_xor_sync(0xffffffffu, c1, m);
+        const float t2 = __shfl_xor_sync(0xffffffffu, s2, m), e2 = __shfl_xor_sync(0xffffffffu, c2, m);
+        if (threadIdx.x & m) {  // lane-order independent: every lane gets the same bits
+            float a1 = t1, b1 = e1, a2 = t2, b2 = e2;
+            stat_merge(a1, b1, a2, b2, s1, c1, s2, c2);
+            s1 = a1, c1 = b1, s2 = a2, c2 = b2;
+        } else {
+            stat_merge(s1, c1, s2, c2, t1, e1, t2, e2);
+        }
+    }
+    if (lane == 0) sh[warp] = StatPartial{s1, c1, s2, c2};
+    __syncthreads();
+    if (warp == 0) {
+        StatPartial p = lane < SD_THREADS / 32 ? sh[lane] : StatPartial{-0.f, 0.f, -0.f, 0.f};
+        s1 = p.s1, c1 = p.c1, s2 = p.s2, c2 = p.c2;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            const float t1 = __shfl_xor_sync(0xffffffffu, s1, m), e1 = __shfl_xor_sync(0xffffffffu, c1, m);
+            const float t2 = __shfl_xor_sync(0xffffffffu, s2, m), e2 = __shfl_xor_sync(0xffffffffu, c2, m);
+            if (threadIdx.x & m) {
+                float a1 = t1, b1 = e1, a2 = t2, b2 = e2;
+                stat_merge(a1, b1, a2, b2, s1, c1, s2, c2);
+                s1 = a1, c1 = b1, s2 = a2, c2 = b2;
+            } else {
+                stat_merge(s1, c1, s2, c2, t1, e1, t2, e2);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+struct StdArgs {
+    const float *x;
+    float *y;
+    int64_t n;
+    double *stats;          // device [mean, var] for the caller
+    StatPartial *partials;  // [grid]
+    unsigned *counter;      // pass-1 arrivals (zero on entry and exit)
+    unsigned *flag;         // generation published by the last CTA
+    StdShared *shared;      // statistics for pass 2
+    int *err;
+    unsigned gen;
+    int fused;              // 1: wait for the statistics and run pass 2 here
+};
+
+__device__ __forceinline__ void neumaier2(float &s, float &c, float x) { neumaier(s, c, x); }
+
+// x^2 added exactly: p = fl(x*x) through the compensated sum, and the product's
+// rounding error e = x*x - p (exact by fused multiply-add) into the compensation.
+__device__ __forceinline__ void add_square(float &s, float &c, float x) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    neumaier(s, c, p);
+    c = __fadd_rn(c, e);
+}
+
+__device__ __forceinline__ void publish_stats(const StdArgs &p, const StatPartial *part, int G, StatPartial *sh) {
+    // last CTA: merge all CTA partials in double, in a fixed order
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < G; i += SD_THREADS) {
+        const uint4 raw = __ldcg(reinterpret_cast<const uint4 *>(part + i));
+        a += (double)__uint_as_float(raw.x) + (double)__uint_as_float(raw.y);
+        b += (double)__uint_as_float(raw.z) + (double)__uint_as_float(raw.w);
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, m);
+        b += __shfl_xor_sync(0xffffffffu, b, m);
+    }
+    __shared__ double sa[SD_THREADS / 32], sb[SD_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < SD_THREADS / 32; ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        const double nn = (double)p.n;
+        const double mean = p.n > 0 ? ta / nn : 0.0;
+        const double var = p.n > 0 ? tb / nn - mean * mean : 0.0;
+        p.shared->mean = mean;
+        p.shared->var = var;
+        p.shared->mean_f = (float)mean;
+        p.shared->rstd_f = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.0f;
+        p.stats[0] = mean;
+        p.stats[1] = var;
+        *p.counter = 0u;
+        __threadfence();
+        st_release(p.flag, p.gen);
+    }
+    (void)sh;
+}
+
+__device__ __forceinline__ void map_pass(const float *x, float *y, int64_t n, float mean_f, float rstd_f) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const bool al = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+    if (al) {
+        const int64_t nv = n / 4;
+        const float4 *x4 = (const float4 *)x;
+        float4 *y4 = (float4 *)y;
+        for (int64_t v = gtid; v < nv; v += nth) {
+            float4 a = x4[v];
+            a.x = __fmul_rn(__fsub_rn(a.x, mean_f), rstd_f);
+            a.y = __fmul_rn(__fsub_rn(a.y, mean_f), rstd_f);
+            a.z = __fmul_rn(__fsub_rn(a.z, mean_f), rstd_f);
+            a.w = __fmul_rn(__fsub_rn(a.w, mean_f), rstd_f);
+            y4[v] = a;
+        }
+        for (int64_t i = 4 * nv + gtid; i < n; i += nth) y[i] = __fmul_rn(__fsub_rn(x[i], mean_f), rstd_f);
+    } else {
+        for (int64_t i = gtid; i < n; i += nth) y[i] = __fmul_rn(__fsub_rn(x[i], mean_f), rstd_f);
+    }
+}
+
+__global__ void __launch_bounds__(SD_THREADS) standardize_kernel(const __grid_constant__ StdArgs p) {
+    __shared__ StatPartial sh[SD_THREADS / 32];
+    __shared__ int am_last;
+    float s1 = -0.f, c1 = 0.f, s2 = -0.f, c2 = 0.f;
+    const int64_t gtid = (int64_t)blockIdx.x * SD_THREADS + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * SD_THREADS;
+    const bool al = ((uintptr_t)p.x & 15) == 0;
+    if (al) {
+        const int64_t nv = p.n / 4;
+        const float4 *x4 = (const float4 *)p.x;
+        for (int64_t v = gtid; v < nv; v += nth) {
+            const float4 a = __ldg(x4 + v);
+            neumaier2(s1, c1, a.x);
+            add_square(s2, c2, a.x);
+            neumaier2(s1, c1, a.y);
+            add_square(s2, c2, a.y);
+            neumaier2(s1, c1, a.z);
+            add_square(s2, c2, a.z);
+            neumaier2(s1, c1, a.w);
+            add_square(s2, c2, a.w);
+        }
+        for (int64_t i = 4 * nv + gtid; i < p.n; i += nth) {
+            const float a = p.x[i];
+            neumaier2(s1, c1, a);
+            add_square(s2, c2, a);
+        }
+    } else {
+        for (int64_t i = gtid; i < p.n; i += nth) {
+            const float a = p.x[i];
+            neumaier2(s1, c1, a);
+            add_square(s2, c2, a);
+        }
+    }
+    stat_cta(s1, c1, s2, c2, sh);
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        p.partials[blockIdx.x] = StatPartial{s1, c1, s2, c2};
+        __threadfence();
+        am_last = atomicAdd(p.counter, 1u) == (unsigned)G - 1u;
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        publish_stats(p, p.partials, G, sh);
+    }
+    if (!p.fused) return;
+    // every CTA waits (bounded) for the statistics, then runs the elementwise pass
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        uint32_t i = 0;
+        int ok = 1;
+        while (ld_acquire(p.flag) != p.gen) {
+            if (++i > kSpinLimit) {
+                ok = 0;
+                atomicExch(p.err, 6);
+                break;
+            }
+            __nanosleep(64);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    __threadfence();
+    const float mean_f = *(volatile float *)&p.shared->mean_f;
+    const float rstd_f = *(volatile float *)&p.shared->rstd_f;
+    map_pass(p.x, p.y, p.n, mean_f, rstd_f);
+}
+
+__global__ void map_kernel(const float *x, float *y, int64_t n, const StdShared *st, float mean_f, float rstd_f,
+                           int from_device) {
+    if (from_device) {
+        mean_f = st->mean_f;
+        rstd_f = st->rstd_f;
+    }
+    map_pass(x, y, n, mean_f, rstd_f);
+}
+
+// ============================================================================
+// BFS pattern: level-synchronous search on a grid with a convergence flag
+// ============================================================================
+
+constexpr int BF_THREADS = 256;
+
+__global__ void bfs_init_kernel(int32_t *dist, int64_t total, int64_t src, const uint8_t *open) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x)
+        dist[c] = (c == src && open[c]) ? 0 : -1;
+}
+
+// One level, pull form: an unvisited open cell with a neighbour at level L
+// joins level L + 1.  Returns whether this thread changed any cell.
+__device__ __forceinline__ bool bfs_level(const uint8_t *__restrict__ open, int32_t *dist, int64_t rows,
+                                          int64_t cols, int32_t L) {
+    const int64_t total = rows * cols;
+    bool changed = false;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldcg(dist + c) != -1 || !__ldg(open + c)) continue;
+        const int64_t r = c / cols, q = c - r * cols;
+        const bool hit = (r > 0 && __ldcg(dist + c - cols) == L) || (r + 1 < rows && __ldcg(dist + c + cols) == L) ||
+                         (q > 0 && __ldcg(dist + c - 1) == L) || (q + 1 < cols && __ldcg(dist + c + 1) == L);
+        if (hit) {
+            dist[c] = L + 1;
+            changed = true;
+        }
+    }
+    return changed;
+}
+
+// mode 0: `||` reduction of the flag (warp vote, CTA vote, last-CTA merge)
+// mode 1: guarded write (the flag was cleared; threads only write 1)
+__global__ void __launch_bounds__(BF_THREADS) bfs_level_kernel(const uint8_t *__restrict__ open, int32_t *dist,
+                                                               int64_t rows, int64_t cols, int32_t L, int mode,
+                                                               unsigned *more, unsigned *partial, unsigned *counter) {
+    const bool changed = bfs_level(open, dist, rows, cols, L);
+    if (mode == 1) {
+        if (changed) *more = 1u;
+        return;
+    }
+    const int any = __syncthreads_or(changed ? 1 : 0);
+    __shared__ int am_last;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = (unsigned)any;
+        __threadfence();
+        am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    int v = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += BF_THREADS) v |= (int)__ldcg(partial + b);
+    v = __syncthreads_or(v);
+    if (threadIdx.x == 0) {
+        *more = (unsigned)(v != 0);
+        *counter = 0u;
+    }
+}
+
+// All levels in one cooperative launch: per level, the || of the changed
+// flags goes to a per-level slot, a bounded grid barrier separates levels.
+__global__ void __launch_bounds__(BF_THREADS) bfs_persistent_kernel(const uint8_t *__restrict__ open, int32_t *dist,
+                                                                    int64_t rows, int64_t cols, unsigned *flags,
+                                                                    int64_t max_levels, unsigned *bar,
+                                                                    int64_t *levels_out, int *err) {
+    unsigned gen = *(volatile unsigned *)&bar[1];
+    int64_t L = 0;
+    for (; L < max_levels; ++L) {
+        const bool changed = bfs_level(open, dist, rows, cols, (int32_t)L);
+        const int any = __syncthreads_or(changed ? 1 : 0);
+        if (threadIdx.x == 0 && any) atomicOr(&flags[L & 1], 1u);
+        if (!grid_barrier(bar, gen)) {
+            if (threadIdx.x == 0) atomicExch(err, 7);
+            return;
+        }
+        const unsigned f = *(volatile unsigned *)&flags[L & 1];
+        // clear the other slot for the next level; every CTA has read it already
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(L + 1) & 1] = 0u;
+        if (!grid_barrier(bar, gen)) {
+            if (threadIdx.x == 0) atomicExch(err, 7);
+            return;
+        }
+        if (!f) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *levels_out = L + 1;  // the level that found nothing new
+}
+
+}  // namespace accr
+
+using namespace accr;
+
+// ---- Nearest Neighbor ------------------------------------------------------------
+
+extern "C" ACCR_API int accr_nearest_k(const float *pts, int64_t n, float qx, float qy, int32_t k,
+                                       int64_t *idx_out, float *d2_out, uint32_t flags, accr_stream_t stream) {
+    clear_error();
+    if (n < 0 || k < 1 || k > 16) return set_error(ACCR_EINVAL, "accr_nearest_k: need n >= 0 and 1 <= k <= 16");
+    if (flags & ~ACCR_SYNC) return set_error(ACCR_EINVAL, "accr_nearest_k: unsupported flags 0x%x", flags);
+    if ((n > 0 && !pts) || !idx_out || !d2_out) return set_error(ACCR_EINVAL, "accr_nearest_k: NULL pointer");
+    if (((uintptr_t)pts & 7) || ((uintptr_t)idx_out & 7) || ((uintptr_t)d2_out & 3))
+        return set_error(ACCR_EINVAL, "accr_nearest_k: misaligned pointer (points need 8 bytes)");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = k <= 8 ? nearest_launch<8>(pts, n, qx, qy, k, idx_out, d2_out, s)
+                    : nearest_launch<16>(pts, n, qx, qy, k, idx_out, d2_out, s);
+    if (rc != ACCR_OK) return rc;
+    if (flags & ACCR_SYNC) return cuda_check(cudaStreamSynchronize(s), "accr_nearest_k: sync");
+    return ACCR_OK;
+}
+
+// ---- SRAD pattern -------------------------------------------------------------------
+
+struct StdState {
+    std::mutex mu;
+    unsigned gen = 0;
+};
+static StdState g_std;
+
+extern "C" ACCR_API int accr_standardize(const float *x, int64_t n, float *y, double *stats, uint32_t flags,
+                                         accr_stream_t stream) {
+    clear_error();
+    if (n < 0 || (n > 0 && (!x || !y)) || !stats) return set_error(ACCR_EINVAL, "accr_standardize: bad arguments");
+    if (((uintptr_t)x & 3) || ((uintptr_t)y & 3) || ((uintptr_t)stats & 7))
+        return set_error(ACCR_EINVAL, "accr_standardize: misaligned pointer");
+    if (flags & ~(ACCR_SYNC | ACCR_UNFUSED | ACCR_TWO_LEVEL_HOST))
+        return set_error(ACCR_EINVAL, "accr_standardize: unsupported flags 0x%x", flags);
+    cudaStream_t s = (cudaStream_t)stream;
+    const DeviceInfo &di = device_info();
+    static int per_sm = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, standardize_kernel, SD_THREADS, 0);
+        if (per_sm < 1) per_sm = 1;
+    });
+    const int64_t want = (n / 4 + SD_THREADS * 4 - 1) / (SD_THREADS * 4);
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
+    // scratch: [counters][partials][shared stats][status]
+    Scratch *scr = scratch_for(stream, sizeof(StatPartial) * (size_t)grid + 256);
+    if (!scr) return ACCR_ENOMEM;
+    StdArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = x;
+    a.y = y;
+    a.n = n;
+    a.stats = stats;
+    a.partials = (StatPartial *)((char *)scr->buf + 256);
+    a.counter = scr->counters + 2;
+    a.flag = scr->counters + 3;
+    a.shared = (StdShared *)scr->buf;
+    a.err = (int *)(scr->counters + 4);
+    {
+        std::lock_guard<std::mutex> lk(g_std.mu);
+        a.gen = ++g_std.gen;
+        if (a.gen == 0) a.gen = ++g_std.gen;
+    }
+    int rc = cuda_check(cudaMemsetAsync(a.err, 0, sizeof(int), s), "accr_standardize: clear status");
+    if (rc != ACCR_OK) return rc;
+    if ((rc = launch_guard("standardize_kernel")) != ACCR_OK) return rc;
+    if (flags & ACCR_TWO_LEVEL_HOST) {
+        // the paper's form: CTA partials to the host, merged there, then the
+        // elementwise region with the statistics as launch arguments
+        a.fused = 0;
+        standardize_kernel<<<grid, SD_THREADS, 0, s>>>(a);
+        if ((rc = launched("standardize_kernel")) != ACCR_OK) return rc;
+        StatPartial *h = (StatPartial *)host_staging_for(stream, sizeof(StatPartial) * (size_t)grid);
+        if (!h) return ACCR_ENOMEM;
+        rc = cuda_check(cudaMemcpyAsync(h, a.partials, sizeof(StatPartial) * (size_t)grid, cudaMemcpyDeviceToHost, s),
+                        "accr_standardize: partials");
+        if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "accr_standardize: sync");
+        if (rc != ACCR_OK) return rc;
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < grid; ++i) {
+            ta += (double)h[i].s1 + (double)h[i].c1;
+            tb += (double)h[i].s2 + (double)h[i].c2;
+        }
+        const double mean = n > 0 ? ta / (double)n : 0.0, var = n > 0 ? tb / (double)n - mean * mean : 0.0;
+        const float mean_f = (float)mean, rstd_f = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.0f;
+        map_kernel<<<di.sms * 4, 512, 0, s>>>(x, y, n, nullptr, mean_f, rstd_f, 0);
+        if ((rc = launched("map_kernel")) != ACCR_OK) return rc;
+        const double st[2] = {mean, var};
+        rc = cuda_check(cudaMemcpyAsync(stats, st, sizeof st, cudaMemcpyHostToDevice, s), "accr_standardize: stats");
+        if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "accr_standardize: sync");
+        return rc;
+    }
+    if (flags & ACCR_UNFUSED) {
+        // two launches, the statistics stay on the device
+        a.fused = 0;
+        standardize_kernel<<<grid, SD_THREADS, 0, s>>>(a);
+        if ((rc = launched("standardize_kernel")) != ACCR_OK) return rc;
+        map_kernel<<<di.sms * 4, 512, 0, s>>>(x, y, n, a.shared, 0.f, 0.f, 1);
+        if ((rc = launched("map_kernel")) != ACCR_OK) return rc;
+    } else {
+        // one cooperative launch: co-residency of every CTA is guaranteed, so
+        // the wait for the statistics cannot starve the CTA that publishes them
+        a.fused = 1;
+        void *args[] = {&a};
+        rc = cuda_check(cudaLaunchCooperativeKernel((const void *)standardize_kernel, grid, SD_THREADS, args, 0, s),
+                        "accr_standardize: cooperative launch");
+        if (rc != ACCR_OK) return rc;
+        if ((rc = launched("standardize_kernel (fused)")) != ACCR_OK) return rc;
+    }
+    if (flags & ACCR_SYNC) {
+        int h = 0;
+        rc = cuda_check(cudaMemcpyAsync(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost, s), "accr_standardize: status");
+        if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "accr_standardize: sync");
+        if (rc == ACCR_OK && h != 0) return set_error(ACCR_ETIMEDOUT, "accr_standardize: grid wait ran out");
+    }
+    return rc;
+}
+
+// ---- BFS pattern -------------------------------------------------------------------
+
+extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t cols, int64_t src, int32_t *dist,
+                                      int32_t mode, int64_t *levels, accr_stream_t stream) {
+    clear_error();
+    if (rows < 0 || cols < 0 || (rows * cols > 0 && (!open || !dist)) || !levels)
+        return set_error(ACCR_EINVAL, "accr_grid_bfs: bad arguments");
+    if (rows * cols >= ((int64_t)1 << 31)) return set_error(ACCR_EINVAL, "accr_grid_bfs: grid too large");
+    if (mode < ACCR_BFS_REDUCE || mode > ACCR_BFS_PERSISTENT) return set_error(ACCR_EINVAL, "accr_grid_bfs: bad mode");
+    *levels = 0;
+    const int64_t total = rows * cols;
+    if (total == 0) return ACCR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const DeviceInfo &di = device_info();
+    int rc;
+    if ((rc = launch_guard("bfs_init_kernel")) != ACCR_OK) return rc;
+    bfs_init_kernel<<<di.sms * 4, 256, 0, s>>>(dist, total, (src >= 0 && src < total) ? src : -1, open);
+    if ((rc = launched("bfs_init_kernel")) != ACCR_OK) return rc;
+    if (src < 0 || src >= total) return cuda_check(cudaStreamSynchronize(s), "accr_grid_bfs: sync");
+    {  // a closed source cell reaches nothing: zero levels
+        uint8_t o = 0;
+        rc = cuda_check(cudaMemcpyAsync(&o, open + src, 1, cudaMemcpyDeviceToHost, s), "accr_grid_bfs: source");
+        if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "accr_grid_bfs: sync");
+        if (rc != ACCR_OK) return rc;
+        if (!o) return ACCR_OK;
+    }
+    static int per_sm = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_persistent_kernel, BF_THREADS, 0);
+        if (per_sm < 1) per_sm = 1;
+    });
+    const int64_t want = (total + BF_THREADS - 1) / BF_THREADS;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)per_sm * di.sms);
+    Scratch *scr = scratch_for(stream, sizeof(unsigned) * (size_t)grid + 512);
+    if (!scr) return ACCR_ENOMEM;
+    unsigned *more = scr->counters + 8;
+    unsigned *counter = scr->counters + 9;
+    unsigned *flags2 = scr->counters + 10;   // two level slots
+    unsigned *bar = scr->counters + 12;      // arrivals, generation
+    int *err = (int *)(scr->counters + 14);
+    int64_t *lv = (int64_t *)((char *)scr->buf);
+    unsigned *partial = (unsigned *)((char *)scr->buf + 64);
+    unsigned *hmore = (unsigned *)host_staging_for(stream, 64);
+    if (!hmore) return ACCR_ENOMEM;
+    if (mode == ACCR_BFS_PERSISTENT) {
+        rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_grid_bfs: clear status");
+        if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(flags2, 0, 2 * sizeof(unsigned), s), "accr_grid_bfs: flags");
+        if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(bar, 0, sizeof(unsigned), s), "accr_grid_bfs: barrier");
+        if (rc != ACCR_OK) return rc;
+        int64_t maxl = total + 1;
+        void *args[] = {(void *)&open, (void *)&dist, (void *)&rows, (void *)&cols, (void *)&flags2, (void *)&maxl,
+                        (void *)&bar, (void *)&lv, (void *)&err};
+        if ((rc = launch_guard("bfs_persistent_kernel")) != ACCR_OK) return rc;
+        rc = cuda_check(cudaLaunchCooperativeKernel((const void *)bfs_persistent_kernel, grid, BF_THREADS, args, 0, s),
+                        "accr_grid_bfs: cooperative launch");
+        if (rc != ACCR_OK) return rc;
+        if ((rc = launched("bfs_persistent_kernel")) != ACCR_OK) return rc;
+        int64_t hl[2] = {0, 0};
+        rc = cuda_check(cudaMemcpyAsync(hl, lv, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "accr_grid_bfs: levels");
+        int herr = 0;
+        if (rc == ACCR_OK)
+            rc = cuda_check(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s), "accr_grid_bfs: status");
+        if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "accr_grid_bfs: sync");
+        if (rc != ACCR_OK) return rc;
+        if (herr) return set_error(ACCR_ETIMEDOUT, "accr_grid_bfs: grid barrier wait ran out");
+        *levels = hl[0];
+        return ACCR_OK;
+    }
+    // host-driven levels: one launch per level, the flag read back after each
+    for (int64_t L = 0; L <= total; ++L) {
+        if (mode == ACCR_BFS_GUARDED) {
+            rc = cuda_check(cudaMemsetAsync(more, 0, sizeof(unsigned), s), "accr_grid_bfs: clear flag");
+            if (rc != ACCR_OK) return rc;
+        }
+        if ((rc = launch_guard("bfs_level_kernel")) != ACCR_OK) return rc;
+        bfs_level_kernel<<<grid, BF_THREADS, 0, s>>>(open, dist, rows, cols, (int32_t)L,
+                                                     mode == ACCR_BFS_GUARDED ? 1 : 0, more, partial, counter);
+        if ((rc = launched("bfs_level_kernel")) != ACCR_OK) return rc;
+        rc = cuda_check(cudaMemcpyAsync(hmore, more, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "accr_grid_bfs: flag");
+        if (rc == ACCR_OK) rc = cuda_check(cudaStreamSynchronize(s), "accr_grid_bfs: sync");
+        if (rc != ACCR_OK) return rc;
+        if (!*hmore) {
+            *levels = L + 1;
+            return ACCR_OK;
+        }
+    }
+    *levels = total + 1;
+    return ACCR_OK;
+}

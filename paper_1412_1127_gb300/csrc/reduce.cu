@@ -3,9 +3,9 @@
 // i-iii and the cross-block merge of Stage 3.7).
 //
 // Work sharing: gang -> CTA of a persistent grid sized to the SM count,
-// worker -> warp, vector -> lane.  Each thread streams its share with
-// non-allocating 32-byte vector loads (RU in flight per iteration, coalesced
-// across the CTA), folding them into private accumulators.  Warps merge through
+// worker -> warp, vector -> lane.  Each thread streams 16-byte vectors with
+// non-allocating loads (RU vectors in flight per iteration, coalesced across
+// the CTA), folding them into private accumulators.  Warps merge through
 // shuffles, the CTA through shared memory, and each CTA writes one partial per
 // clause.  The last CTA to finish (a counter in library scratch) merges the
 // partials in a fixed order and writes the variables, so there is no second
@@ -21,7 +21,7 @@
 namespace accr {
 
 constexpr int RB = 512;          // threads per CTA
-constexpr int RU = 4;            // 32-byte vectors per thread per iteration
+constexpr int RU = 4;            // 16-byte vectors per thread per iteration
 constexpr int kMaxGrid = 4096;   // bound on CTAs (and partials per clause)
 
 struct ReduceArgs {
@@ -34,15 +34,13 @@ struct ReduceArgs {
     unsigned *counter;           // zero on entry; zero again on exit
 };
 
-// 32-byte streaming load (sm_100+ 256-bit vector): read-only path, no L1
-// allocation, 256-byte L2 fetch; returned as two 16-byte halves.
-struct __align__(32) V32 {
-    uint4 lo, hi;
-};
-__device__ __forceinline__ void ld_stream32(const V32 *p, uint4 &lo, uint4 &hi) {
-    asm("ld.global.nc.L1::no_allocate.L2::256B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+// 16-byte streaming load: read-only path, no L1 allocation, 256-byte L2 fetch.
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(p));
+    return v;
 }
 
 __device__ __forceinline__ Partial ld_partial(const Partial *p) {
@@ -57,15 +55,15 @@ __device__ __forceinline__ Partial ld_partial(const Partial *p) {
 template <typename T, int NC>
 __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ ReduceArgs p) {
     constexpr bool E64 = sizeof(T) == 8;
-    constexpr int EPV = 32 / (int)sizeof(T);  // elements per 32-byte vector
+    constexpr int EPV = 16 / (int)sizeof(T);
     __shared__ Acc sh[NC][RB / 32];
     __shared__ int am_last;
 
     const T *in = (const T *)p.in;
     const int64_t n = p.n;
-    const int64_t mis = (int64_t)(((32 - ((uintptr_t)in & 31)) & 31) / sizeof(T));
-    const int64_t head = mis < n ? mis : n;          // elements before 32-B alignment
-    const V32 *vin = (const V32 *)(in + head);
+    const int64_t mis = (int64_t)(((16 - ((uintptr_t)in & 15)) & 15) / sizeof(T));
+    const int64_t head = mis < n ? mis : n;          // elements before 16-B alignment
+    const uint4 *vin = (const uint4 *)(in + head);
     const int64_t nvec = (n - head) / EPV;
     const int64_t tail0 = head + nvec * EPV;          // ragged tail start
 
@@ -95,20 +93,19 @@ __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ R
     int64_t v = (int64_t)blockIdx.x * (RB * RU) + threadIdx.x;
     const int64_t step = (int64_t)gridDim.x * (RB * RU);
     for (; v + (RU - 1) * RB < nvec; v += step) {
-        uint4 b[2 * RU];
+        uint4 b[RU];
 #pragma unroll
-        for (int u = 0; u < RU; ++u) ld_stream32(vin + v + u * RB, b[2 * u], b[2 * u + 1]);
+        for (int u = 0; u < RU; ++u) b[u] = ld_stream(vin + v + u * RB);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) fold_vec<T, 2 * RU>(w[c], A[c], b);
+        for (int c = 0; c < NC; ++c) fold_vec<T, RU>(w[c], A[c], b);
     }
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
         const int64_t vv = v + u * RB;
         if (vv < nvec) {
-            uint4 b[2];
-            ld_stream32(vin + vv, b[0], b[1]);
+            uint4 b = ld_stream(vin + vv);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) fold_vec<T, 2>(w[c], A[c], b);
+            for (int c = 0; c < NC; ++c) fold_vec<T, 1>(w[c], A[c], &b);
         }
     }
 
@@ -206,7 +203,7 @@ static int grid_for(int nc, int64_t n) {
     case 3: maxg = occupancy_grid<T, 3>(); break;
     default: maxg = occupancy_grid<T, 4>(); break;
     }
-    const int64_t nvec = n * (int64_t)sizeof(T) / 32;
+    const int64_t nvec = n * (int64_t)sizeof(T) / 16;
     int64_t want = (nvec + (int64_t)RB * RU - 1) / ((int64_t)RB * RU);
     if (want < 1) want = 1;
     return (int)(want < maxg ? want : maxg);

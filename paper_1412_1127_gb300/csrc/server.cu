@@ -98,7 +98,7 @@ struct accr_server {
 
     void run();
     void complete(Slot &s, int64_t t);
-    bool launch(Slot &s, std::unique_lock<std::mutex> &lk);
+    int launch(Slot &s, std::unique_lock<std::mutex> &lk);
 };
 
 void accr_server::complete(Slot &s, int64_t t) {
@@ -125,7 +125,9 @@ void accr_server::complete(Slot &s, int64_t t) {
 
 // Forms a batch from the head of the queue (admission by budget, FIFO) and
 // launches it on slot s.  Called with the lock held; drops it while launching.
-bool accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
+// Returns 0 if nothing was admitted, 1 if a batch is in flight, 2 if the
+// batch failed to launch (its requests are already completed with the error).
+int accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
     std::vector<Req> take;
     int64_t bytes = 0;
     while (!pending.empty() && (int)take.size() < max_batch) {
@@ -135,7 +137,7 @@ bool accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
         take.push_back(q);
         pending.pop_front();
     }
-    if (take.empty()) return false;
+    if (take.empty()) return 0;
     inflight += (uint64_t)bytes;
     s.busy = true;
     s.bytes = bytes;
@@ -155,8 +157,11 @@ bool accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
     if (rc == ACCR_OK) rc = cuda_check(cudaEventRecord(s.done, s.stream), "server: event");
     s.status = rc;
     lk.lock();
-    if (rc != ACCR_OK) complete(s, now_ns());
-    return true;
+    if (rc != ACCR_OK) {
+        complete(s, now_ns());
+        return 2;
+    }
+    return 1;
 }
 
 void accr_server::run() {
@@ -180,8 +185,10 @@ void accr_server::run() {
         if (finished) cv_done.notify_all();
         for (Slot &s : slots) {
             if (s.busy || pending.empty()) continue;
-            if (!launch(s, lk)) break;
-            any_busy = true;
+            const int r = launch(s, lk);
+            if (r == 0) break;
+            if (r == 1) any_busy = true;
+            else finished = true;  // failed batch: its waiters must wake up
         }
         if (finished) cv_done.notify_all();
         if (stop && pending.empty() && !any_busy) break;

@@ -1,0 +1,100 @@
+"""Application patterns of the paper (Sec. 4.2) on the GPU against the oracle:
+Nearest Neighbor (k smallest distances), SRAD (a reduction feeding an
+elementwise region), BFS (a convergence loop with an || flag)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1412_1127_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 7, 100, 1001, 65537, (1 << 20) + 3])
+@pytest.mark.parametrize("k", [1, 5, 8, 16])
+def test_nearest_k_exact(n, k):
+    g = inputs.rng(21, n)
+    pts = (g.random((n, 2), dtype=np.float32) * 100).astype(np.float32)
+    if n > 10:
+        pts[n // 2] = pts[n // 3]          # an exact tie, broken by index
+    qx, qy = 41.5, 58.25
+    for off in ([0, 1] if n in (7, 1001) else [0]):
+        big = np.zeros((n + off, 2), dtype=np.float32)
+        big[off:] = pts
+        pt = torch.from_numpy(big).cuda()[off:]
+        idx = torch.empty(k, dtype=torch.int64, device="cuda")
+        d2 = torch.empty(k, dtype=torch.float32, device="cuda")
+        api.accr_nearest_k(pt, qx, qy, k, idx, d2, flags=api.ACCR_SYNC)
+        wi, wd = oracle.nearest_k(pts, qx, qy, k)
+        assert np.array_equal(idx.cpu().numpy(), wi), (n, k, off)
+        assert np.array_equal(d2.cpu().numpy(), wd), (n, k, off)
+
+
+def test_nearest_k_rejects_bad_k():
+    pts = torch.zeros((4, 2), device="cuda")
+    i = torch.empty(32, dtype=torch.int64, device="cuda")
+    d = torch.empty(32, device="cuda")
+    with pytest.raises(api._native.AccrError):
+        api.accr_nearest_k(pts, 0, 0, 17, i, d)
+
+
+@pytest.mark.parametrize("n", [1, 5, 1000, 4 * 1024 * 1024 + 3, 1 << 26])
+@pytest.mark.parametrize("form", ["fused", "unfused", "host"])
+def test_standardize(n, form):
+    x = (inputs.normal(n, np.float32, salt=n % 7) * 3 + 5).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    st = torch.empty(2, dtype=torch.float64, device="cuda")
+    flags = {"fused": 0, "unfused": api.ACCR_UNFUSED, "host": api.ACCR_TWO_LEVEL_HOST}[form] | api.ACCR_SYNC
+    api.accr_standardize(xt, y, st, flags=flags)
+    wy, (wm, wv) = oracle.standardize(x)
+    mean, var = st.cpu().numpy()
+    assert abs(mean - wm) <= 1e-9 * max(abs(wm), 1.0)
+    assert abs(var - wv) <= 1e-9 * max(abs(wv), 1e-30) or n == 1
+    got = y.cpu().numpy()
+    # (x - mean_f) * rstd_f: the float statistics may differ in their last bit
+    assert np.max(np.abs(got - wy) / np.maximum(np.abs(wy), 1.0)) <= 4e-6
+
+
+def test_standardize_in_place_and_repeat():
+    x = inputs.normal(1 << 20, np.float32, salt=3)
+    xt = torch.from_numpy(x.copy()).cuda()
+    st = torch.empty(2, dtype=torch.float64, device="cuda")
+    api.accr_standardize(xt, xt, st, flags=api.ACCR_SYNC)       # y aliases x
+    wy, _ = oracle.standardize(x)
+    assert np.max(np.abs(xt.cpu().numpy() - wy)) <= 4e-6 * max(1.0, float(np.abs(wy).max()))
+    for _ in range(3):                                            # the grid wait re-arms
+        y = torch.empty_like(xt)
+        api.accr_standardize(torch.from_numpy(x).cuda(), y, st, flags=api.ACCR_SYNC)
+
+
+def grid_case(rows, cols, p_open, seed):
+    g = inputs.rng(23, seed)
+    grid = (g.random((rows, cols)) < p_open).astype(np.uint8)
+    src = int(g.integers(0, rows * cols))
+    grid.flat[src] = 1
+    return grid, src
+
+
+@pytest.mark.parametrize("mode", ["reduce", "guarded", "persistent"])
+@pytest.mark.parametrize("shape,p", [((1, 1), 1.0), ((1, 50), 1.0), ((13, 17), 0.7), ((64, 64), 0.6),
+                                     ((300, 200), 0.65), ((1024, 1024), 0.62)])
+def test_grid_bfs_exact(mode, shape, p):
+    grid, src = grid_case(*shape, p, seed=shape[0] * 31 + shape[1])
+    want, wl = oracle.grid_bfs(grid, src)
+    gt = torch.from_numpy(grid).cuda()
+    dist = torch.empty(shape, dtype=torch.int32, device="cuda")
+    levels = api.accr_grid_bfs(gt, src, dist, mode=mode)
+    assert np.array_equal(dist.cpu().numpy(), want)
+    assert levels == wl
+
+
+def test_grid_bfs_closed_source():
+    grid = np.ones((8, 8), dtype=np.uint8)
+    grid.flat[9] = 0
+    gt = torch.from_numpy(grid).cuda()
+    dist = torch.empty((8, 8), dtype=torch.int32, device="cuda")
+    for mode in ["reduce", "guarded", "persistent"]:
+        assert api.accr_grid_bfs(gt, 9, dist, mode=mode) == 0
+        assert bool((dist == -1).all())

@@ -222,3 +222,13 @@ def test_errors_are_reported_not_fatal():
     assert e.value.code == api._native.ACCR_ETYPE
     api.accr_reduce(x, [api.clause("add", o)], flags=api.ACCR_SYNC)  # context still fine
     assert o.item() == 0.0
+
+
+def test_variable_in_pinned_host_memory():
+    x = inputs.full_range_i32((1 << 22) + 5, salt=12)
+    xt = torch.from_numpy(x).cuda()
+    s = torch.zeros(1, dtype=torch.int64).pin_memory()
+    m = torch.zeros(1, dtype=torch.int32).pin_memory()
+    api.accr_reduce(xt, [api.clause("add", s), api.clause("max", m)], flags=api.ACCR_SYNC)
+    assert int(s.item()) == int(oracle.reduce(x, "add", "i64"))
+    assert int(m.item()) == int(oracle.reduce(x, "max", "i32"))
