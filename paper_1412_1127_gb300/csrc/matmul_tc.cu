@@ -11,12 +11,12 @@
 // is accumulated in FP32 in tensor memory (the dropped a_lo b_lo term and the
 // split residuals are of order 2^-16 of |a||b|).
 //
-// Kernel shape: one CTA computes a 128 x 256 block of c with
-// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 256, K = 16).  A TMA
-// producer thread streams 64-wide k slices of the four split operands into a
-// two-stage shared-memory ring (128-byte swizzle, the layout the MMA
+// Kernel shape: one CTA computes a 128 x 224 block of c with
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 224, K = 16).  A TMA
+// producer thread streams 32-wide k slices of the four split operands into a
+// four-stage shared-memory ring (64-byte swizzle, the layout the MMA
 // descriptors expect); an MMA thread waits on each stage's mbarrier, issues
-// the three products for the four 16-wide k steps, and frees the stage with
+// the three products for the two 16-wide k steps, and frees the stage with
 // tcgen05.commit; after the last slice the four warps read the accumulator
 // out of tensor memory (tcgen05.ld 32x32b) and store c.
 //
@@ -36,12 +36,17 @@
 
 namespace accr {
 
-constexpr int TBM = 128, TBN = 256, TBK = 64;
-constexpr int TSTAGES = 2;
-constexpr int A_TILE_BYTES = TBM * TBK * 2;                       // 16 KiB
-constexpr int B_TILE_BYTES = TBN * TBK * 2;                       // 32 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;  // 96 KiB
-constexpr int TMEM_COLS = 256;
+// CTA tile 128 x 224: at LEN 4096 the 19 x 32 = 608 tiles are exactly four
+// waves on 152 SMs (128 x 256 tiles would be 3.4 waves); 32-wide k slices in
+// 64-byte swizzled rows give a four-stage ring in 176 KiB of shared memory.
+constexpr int TBM = 128, TBN = 224, TBK = 32;
+constexpr int TSTAGES = 4;
+constexpr int SWZ = 64;                                           // swizzle span (bytes) = one k-slice row
+constexpr int A_TILE_BYTES = TBM * TBK * 2;                       // 8 KiB
+constexpr int B_TILE_BYTES = TBN * TBK * 2;                       // 14 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;  // 44 KiB
+constexpr int TMEM_COLS = 512;                                    // two accumulators, at columns 0 and 256
+constexpr int GEMM_THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
 constexpr uint32_t kMaxTries = 1u << 24;
 
 // Instruction descriptor (kind::f16): FP32 accumulator, BF16 A and B, both
@@ -50,9 +55,10 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN 
                            ((uint32_t)(TBM >> 4) << 24);
 
 struct TcBars {
-    uint64_t full[TSTAGES];
-    uint64_t empty[TSTAGES];
-    uint64_t done;
+    uint64_t full[TSTAGES];   // stage s loaded (TMA transaction count)
+    uint64_t empty[TSTAGES];  // stage s consumed (MMA commit)
+    uint64_t tfull[2];        // accumulator b complete (MMA commit)
+    uint64_t tempty[2];       // accumulator b drained (one arrival per epilogue warp)
     uint32_t tmem;
     int abort;
 };
@@ -89,15 +95,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO), descriptor version 1.
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row
+// groups 8 x 64 = 512 bytes apart (SBO), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-    d |= (uint64_t)1 << 46;            // version
-    d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * SWZ) >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;                  // version
+    d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
     return d;
 }
 
@@ -126,15 +132,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent: one CTA per SM walks the tiles tile = blockIdx.x, +gridDim.x, ...
+// The k-slice ring runs on across tiles; the accumulator alternates between
+// two tensor-memory buffers so the epilogue of one tile overlaps the main
+// loop of the next.
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
     bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                        const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
-                       float *__restrict__ C, int M, int N, int Kp, int *err) {
+                       float *__restrict__ C, int M, int N, int Kp, int tiles_n, int ntiles, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     TcBars *bars = (TcBars *)(smem + TSTAGES * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
     const int nkb = Kp / TBK;
 
     if (threadIdx.x == 0) {
@@ -142,7 +155,10 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(smem_u32(&bars->full[s]), 1);
             mbar_init(smem_u32(&bars->empty[s]), 1);
         }
-        mbar_init(smem_u32(&bars->done), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bars->tfull[b]), 1);
+            mbar_init(smem_u32(&bars->tempty[b]), 4);
+        }
         bars->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -156,83 +172,119 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = bars->tmem;
+    volatile int *abort = &bars->abort;
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
         int issued[TSTAGES];
         for (int s = 0; s < TSTAGES; ++s) issued[s] = -1;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % TSTAGES, use = kb / TSTAGES;
-            if (use > 0 && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((use - 1) & 1))) {
-                atomicExch(err, 1);
-                bars->abort = 1;
-                break;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
+            const int m0 = (tile / tiles_n) * TBM, n0 = (tile % tiles_n) * TBN;
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % TSTAGES, use = it / TSTAGES;
+                if (use > 0 && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((use - 1) & 1))) {
+                    atomicExch(err, 1);
+                    *abort = 1;
+                    break;
+                }
+                if (*abort) break;
+                uint8_t *st = smem + s * STAGE_BYTES;
+                const uint32_t fb = smem_u32(&bars->full[s]);
+                mbar_expect_tx(fb, STAGE_BYTES);
+                tma_load_2d(smem_u32(st), &tAh, kb * TBK, m0, fb);
+                tma_load_2d(smem_u32(st + A_TILE_BYTES), &tAl, kb * TBK, m0, fb);
+                tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES), &tBh, kb * TBK, n0, fb);
+                tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES + B_TILE_BYTES), &tBl, kb * TBK, n0, fb);
+                issued[s] = use;
             }
-            if (*(volatile int *)&bars->abort) break;
-            uint8_t *st = smem + s * STAGE_BYTES;
-            const uint32_t fb = smem_u32(&bars->full[s]);
-            mbar_expect_tx(fb, STAGE_BYTES);
-            tma_load_2d(smem_u32(st), &tAh, kb * TBK, m0, fb);
-            tma_load_2d(smem_u32(st + A_TILE_BYTES), &tAl, kb * TBK, m0, fb);
-            tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES), &tBh, kb * TBK, n0, fb);
-            tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES + B_TILE_BYTES), &tBl, kb * TBK, n0, fb);
-            issued[s] = use;
         }
         // let every copy this thread issued land before the CTA can exit
         for (int s = 0; s < TSTAGES; ++s)
             if (issued[s] >= 0 && !mbar_wait(smem_u32(&bars->full[s]), (uint32_t)(issued[s] & 1))) atomicExch(err, 2);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % TSTAGES, use = kb / TSTAGES;
-            if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)(use & 1))) {
-                atomicExch(err, 3);
-                bars->abort = 1;
+        int it = 0, j = 0;
+        for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++j) {
+            const int b = j & 1, u = j >> 1;
+            if (u > 0 && !mbar_wait(smem_u32(&bars->tempty[b]), (uint32_t)((u - 1) & 1))) {
+                atomicExch(err, 5);
+                *abort = 1;
                 break;
             }
-            if (*(volatile int *)&bars->abort) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t ah = st, al = st + A_TILE_BYTES;
-            const uint32_t bh = st + 2 * A_TILE_BYTES, bl = bh + B_TILE_BYTES;
+            const uint32_t acc = tmem + (uint32_t)(b * 256);
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % TSTAGES, use = it / TSTAGES;
+                if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)(use & 1))) {
+                    atomicExch(err, 3);
+                    *abort = 1;
+                    ok = false;
+                    break;
+                }
+                if (*abort) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t ah = st, al = st + A_TILE_BYTES;
+                const uint32_t bh = st + 2 * A_TILE_BYTES, bl = bh + B_TILE_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < TBK / 16; ++kk) {
-                const uint32_t off = kk * 32;  // 16 bf16 along K inside the 128-byte swizzle atom
-                mma_bf16(tmem, smem_desc(ah + off), smem_desc(bh + off), (kb > 0 || kk > 0) ? 1u : 0u);
-                mma_bf16(tmem, smem_desc(ah + off), smem_desc(bl + off), 1u);
-                mma_bf16(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);
+                for (int kk = 0; kk < TBK / 16; ++kk) {
+                    const uint32_t off = kk * 32;  // 16 bf16 along K inside the 64-byte swizzle row
+                    mma_bf16(acc, smem_desc(ah + off), smem_desc(bh + off), (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(acc, smem_desc(ah + off), smem_desc(bl + off), 1u);
+                    mma_bf16(acc, smem_desc(al + off), smem_desc(bh + off), 1u);
+                }
+                mma_commit(smem_u32(&bars->empty[s]));
             }
-            mma_commit(smem_u32(&bars->empty[s]));
+            mma_commit(smem_u32(&bars->tfull[b]));  // fires when this tile's MMAs are complete
+            if (!ok) break;
         }
-        mma_commit(smem_u32(&bars->done));  // fires when every MMA issued above is complete
+    } else if (warp >= 2) {
+        // ---- epilogue: accumulator lanes 32*q .. +31 (q = warp % 4) to c ----
+        const int q = warp & 3;
+        const bool vec = (N % 4 == 0) && (((uintptr_t)C & 15) == 0);
+        int j = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+            const int b = j & 1, u = j >> 1;
+            const bool ready = mbar_wait(smem_u32(&bars->tfull[b]), (uint32_t)(u & 1));
+            if (!ready) {
+                if (lane == 0) atomicExch(err, 4);
+                *abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool store = !*abort;
+            const int m0 = (tile / tiles_n) * TBM, n0 = (tile % tiles_n) * TBN;
+            const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int ch = 0; ch < TBN / 32; ++ch) {
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t)(b * 256) + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), r);
+                if (!store || row >= M) continue;
+                const int col = n0 + ch * 32;
+                float *dst = C + (size_t)row * (size_t)N + col;
+                if (vec && col + 32 <= N) {
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4)
+                        *reinterpret_cast<float4 *>(dst + e) =
+                            make_float4(__uint_as_float(r[e]), __uint_as_float(r[e + 1]), __uint_as_float(r[e + 2]),
+                                        __uint_as_float(r[e + 3]));
+                } else {
+                    for (int e = 0; e < 32; ++e)
+                        if (col + e < N) dst[e] = __uint_as_float(r[e]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[b]));  // buffer b may be overwritten
+            if (*abort) break;
+        }
     }
     __syncwarp();
-
-    // ---- epilogue: accumulator rows 32*warp .. +31 to c ----
-    bool ready = mbar_wait(smem_u32(&bars->done), 0);
-    if (!ready) atomicExch(err, 4);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool store = ready && !*(volatile int *)&bars->abort;
-    const int row = m0 + warp * 32 + lane;
-    const bool vec = (N % 4 == 0) && (((uintptr_t)C & 15) == 0);
-#pragma unroll 1
-    for (int ch = 0; ch < TBN / 32; ++ch) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), r);
-        if (!store || row >= M) continue;
-        const int col = n0 + ch * 32;
-        float *dst = C + (size_t)row * (size_t)N + col;
-        if (vec && col + 32 <= N) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<float4 *>(dst + j) =
-                    make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                __uint_as_float(r[j + 3]));
-        } else {
-            for (int j = 0; j < 32; ++j)
-                if (col + j < N) dst[j] = __uint_as_float(r[j]);
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -262,37 +314,68 @@ __global__ void wait_selftest_kernel(uint32_t tries, int *err) {
     }
 }
 
-// hi = bf16(x), lo = bf16(x - hi); a row-major M x K -> [M][Kp] (zero padded)
+__device__ __forceinline__ void split2(float x, __nv_bfloat16 &h, __nv_bfloat16 &l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(h)));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// hi = bf16(x), lo = bf16(x - hi); a row-major M x K -> [M][Kp] (zero padded).
+// Each thread splits 8 consecutive elements of a row and stores 16 bytes of
+// hi and of lo.
 __global__ void split_rows_kernel(const float *__restrict__ a, int64_t M, int64_t K, int64_t Kp,
                                   __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
-    const int64_t total = M * Kp;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / Kp, k = i - r * Kp;
-        const float x = k < K ? a[r * K + k] : 0.f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        hi[i] = h;
-        lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    const int64_t k8 = Kp / 8, total = M * k8;
+    const bool vec = (K % 4 == 0) && (((uintptr_t)a & 15) == 0);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / k8, k0 = (t - r * k8) * 8;
+        float x[8];
+        if (vec && k0 + 8 <= K) {
+            const float4 u = __ldg(reinterpret_cast<const float4 *>(a + r * K + k0));
+            const float4 w = __ldg(reinterpret_cast<const float4 *>(a + r * K + k0 + 4));
+            x[0] = u.x, x[1] = u.y, x[2] = u.z, x[3] = u.w, x[4] = w.x, x[5] = w.y, x[6] = w.z, x[7] = w.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = (k0 + e < K) ? a[r * K + k0 + e] : 0.f;
+        }
+        __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split2(x[e], h[e], l[e]);
+        *reinterpret_cast<uint4 *>(hi + r * Kp + k0) =
+            make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+        *reinterpret_cast<uint4 *>(lo + r * Kp + k0) =
+            make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
     }
 }
 
-// b row-major K x N -> transposed split [N][Kp] (zero padded), 32 x 32 tiles
-__global__ void split_cols_kernel(const float *__restrict__ b, int64_t K, int64_t N, int64_t Kp,
-                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
-    __shared__ float tile[32][33];
-    const int64_t k0 = (int64_t)blockIdx.y * 32, n0 = (int64_t)blockIdx.x * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t k = k0 + r, n = n0 + threadIdx.x;
-        tile[r][threadIdx.x] = (k < K && n < N) ? b[k * N + n] : 0.f;
+// b row-major K x N -> transposed split [N][Kp] (zero padded), 64 x 64 tiles
+// through shared memory; each thread then stores 8 consecutive k of one n.
+__global__ void __launch_bounds__(256) split_cols_kernel(const float *__restrict__ b, int64_t K, int64_t N,
+                                                         int64_t Kp, __nv_bfloat16 *__restrict__ hi,
+                                                         __nv_bfloat16 *__restrict__ lo) {
+    __shared__ float tile[64][65];
+    const int64_t k0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+    for (int r = ty; r < 64; r += 4) {
+        const int64_t k = k0 + r, n = n0 + tx;
+        tile[r][tx] = (k < K && n < N) ? __ldg(b + k * N + n) : 0.f;
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t n = n0 + r, k = k0 + threadIdx.x;
-        if (n < N && k < Kp) {
-            const float x = tile[threadIdx.x][r];
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            hi[n * Kp + k] = h;
-            lo[n * Kp + k] = __float2bfloat16_rn(x - __bfloat162float(h));
-        }
+    // 64 n x 8 groups of 8 k = 512 stores of 16 bytes, two per thread
+    for (int g = threadIdx.x; g < 512; g += 256) {
+        const int nn = g >> 3, kg = (g & 7) * 8;
+        const int64_t n = n0 + nn, k = k0 + kg;
+        if (n >= N || k >= Kp) continue;
+        __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split2(tile[kg + e][nn], h[e], l[e]);
+        *reinterpret_cast<uint4 *>(hi + n * Kp + k) =
+            make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+        *reinterpret_cast<uint4 *>(lo + n * Kp + k) =
+            make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
     }
 }
 
@@ -314,7 +397,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D bf16 map over [rows][Kp], box {64, box_rows}, 128-byte swizzle.
+// 2-D bf16 map over [rows][Kp], box {32, box_rows}, 64-byte swizzle.
 static int make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t Kp, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return set_error(ACCR_ECUDA, "accr_matmul_nest: cuTensorMapEncodeTiled unavailable");
@@ -323,7 +406,7 @@ static int make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t Kp, 
     cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ACCR_ECUDA, "accr_matmul_nest: tensor map encode failed (%d)", (int)r);
     return ACCR_OK;
@@ -376,8 +459,8 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     const DeviceInfo &di = device_info();
     split_rows_kernel<<<di.sms * 8, 256, 0, s>>>(a, M, K, Kp, ah, al);
     if ((rc = launched("split_rows_kernel")) != ACCR_OK) return rc;
-    dim3 tg((unsigned)((N + 31) / 32), (unsigned)((Kp + 31) / 32));
-    split_cols_kernel<<<tg, dim3(32, 8), 0, s>>>(b, K, N, Kp, bh, bl);
+    dim3 tg((unsigned)((N + 63) / 64), (unsigned)((Kp + 63) / 64));
+    split_cols_kernel<<<tg, 256, 0, s>>>(b, K, N, Kp, bh, bl);
     if ((rc = launched("split_cols_kernel")) != ACCR_OK) return rc;
     CUtensorMap mah, mal, mbh, mbl;
     if ((rc = make_map(&mah, ah, M, Kp, TBM)) != ACCR_OK) return rc;
@@ -389,8 +472,10 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     std::call_once(attr_once, [smem] {
         cudaFuncSetAttribute(bf16x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
-    dim3 grid((unsigned)((N + TBN - 1) / TBN), (unsigned)((M + TBM - 1) / TBM));
-    bf16x3_gemm_kernel<<<grid, 128, smem, s>>>(mah, mal, mbh, mbl, c, (int)M, (int)N, (int)Kp, err);
+    const int tiles_n = (int)((N + TBN - 1) / TBN), ntiles = tiles_n * (int)((M + TBM - 1) / TBM);
+    const int grid = ntiles < di.sms ? ntiles : di.sms;  // persistent: one CTA per SM
+    bf16x3_gemm_kernel<<<grid, GEMM_THREADS, smem, s>>>(mah, mal, mbh, mbl, c, (int)M, (int)N, (int)Kp, tiles_n,
+                                                        ntiles, err);
     if ((rc = launched("bf16x3_gemm_kernel")) != ACCR_OK) return rc;
     if (sync) {
         int h = 0;
