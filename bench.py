@@ -316,14 +316,30 @@ def run_scalar(args):
         pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
         res_host = torch.empty(R, dtype=torch.int64).pin_memory()
 
+        copy_stream = torch.cuda.Stream(dev)
+        kinds = ("i32", "f32", "f64")
+
         def e2e_step():
-            for kind in ("i32", "f32", "f64"):
-                devin[kind].copy_(pinned[kind], non_blocking=True)
-            step()
+            # each input array is copied in on a copy stream; the regions over
+            # an array start as soon as its copy is done, overlapping the copy
+            # of the next array (host-to-device runs at about 211 GB/s here)
+            ready = {}
+            copy_stream.wait_stream(stream)
+            for kind in kinds:
+                with torch.cuda.stream(copy_stream):
+                    devin[kind].copy_(pinned[kind], non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(copy_stream)
+                ready[kind] = ev
+            for kind in kinds:
+                stream.wait_event(ready[kind])
+                for i, (_, k, _, _, _) in enumerate(SCALAR_REGIONS):
+                    if k == kind:
+                        api.accr_reduce(devin[kind], cls[i], flags=flags[i], stream=stream)
             for i, o in enumerate(outs):
                 res_host[i:i + 1].view(torch.uint8)[: o.element_size()].copy_(
                     o.view(torch.uint8), non_blocking=True)
-            torch.cuda.current_stream(dev).synchronize()
+            stream.synchronize()
 
         e2e_step()
         ek = max(2, min(args.steps, 5))

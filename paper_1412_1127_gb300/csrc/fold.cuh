@@ -211,6 +211,62 @@ __host__ __device__ __forceinline__ void two_sum_merge(float &s, float &c, float
     c = hd_fadd(hd_fadd(c, c2), e);
 }
 
+// Sum of the 2*NV doubles of a chunk.  GB300's FP64 pipe retires about two
+// adds per SM per clock, too few for a double sum at HBM rate, so chunks of
+// 8 or more values are summed in integer block floating point: each
+// significand (with its implicit bit) is aligned to the chunk's largest
+// exponent with 6 guard bits, the aligned magnitudes are added in an int64
+// with their signs, and the total is converted and scaled by an exact power
+// of two -- three FP64-pipe operations per chunk instead of one per value.
+// Bits shifted out are truncated: at most 2^-6 of the largest value's ulp per
+// element (under 0.25 ulp for a chunk of 16).  Chunks whose largest exponent
+// is within 60 of the subnormal range, and short chunks, are added as
+// doubles.  Finite inputs only.
+template <int NV>
+__device__ __forceinline__ double chunk_sum_f64(const uint4 *v) {
+    constexpr int E = 2 * NV;
+    uint64_t b[E];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        b[2 * i] = word64(v[i], 0);
+        b[2 * i + 1] = word64(v[i], 1);
+    }
+    if constexpr (E < 8) {
+        double t = u2d(b[0]);
+#pragma unroll
+        for (int j = 1; j < E; ++j) t = __dadd_rn(t, u2d(b[j]));
+        return t;
+    } else {
+        int ex[E];
+        int emax = 1;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            ex[j] = (int)((b[j] >> 52) & 0x7ffu);
+            emax = ex[j] > emax ? ex[j] : emax;
+        }
+        if (emax < 61) {  // tiny values: the scale below would leave the normal range
+            double t = u2d(b[0]);
+#pragma unroll
+            for (int j = 1; j < E; ++j) t = __dadd_rn(t, u2d(b[j]));
+            return t;
+        }
+        int64_t S = 0;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            uint64_t m = b[j] & 0x000FFFFFFFFFFFFFull;
+            int e = ex[j];
+            if (e) m |= 0x0010000000000000ull;
+            else e = 1;
+            const int sh = emax - e;
+            const int64_t mag = sh < 64 ? (int64_t)((m << 6) >> sh) : 0;
+            S += (b[j] >> 63) ? -mag : mag;
+        }
+        // S counts units of 2^(emax - 1075 - 6); that power of two is normal here
+        const double scale = u2d((uint64_t)(emax - 1081 + 1023) << 52);
+        return __dmul_rn(__ll2double_rn((long long)S), scale);
+    }
+}
+
 // ---- per-element folding -------------------------------------------------------
 // Fold NV 16-byte vectors of T into A under working code w (warp-uniform).
 template <typename T, int NV>
@@ -284,20 +340,7 @@ __device__ __forceinline__ void fold_vec(int w, Acc &A, const uint4 *v) {
                 for_each_elem<T, NV>(v, [&](T x) { a = a + x; });
                 A.a = f2u(a);
             } else {
-                // double: the chunk is summed as a pairwise tree, then added
-                // (as many adds as a chain, but a dependency depth of log2 +1,
-                // which keeps the FP64 pipe fed)
-                double e[2 * NV];
-#pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    e[2 * i] = u2d(word64(v[i], 0));
-                    e[2 * i + 1] = u2d(word64(v[i], 1));
-                }
-#pragma unroll
-                for (int w = 1; w < 2 * NV; w *= 2)
-#pragma unroll
-                    for (int i = 0; i + w < 2 * NV; i += 2 * w) e[i] = __dadd_rn(e[i], e[i + w]);
-                A.a = d2u(__dadd_rn(u2d(A.a), e[0]));
+                A.a = d2u(__dadd_rn(u2d(A.a), chunk_sum_f64<NV>(v)));
             }
         } break;
         case W_ADDF_COMP: {

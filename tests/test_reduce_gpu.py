@@ -232,3 +232,56 @@ def test_variable_in_pinned_host_memory():
     api.accr_reduce(xt, [api.clause("add", s), api.clause("max", m)], flags=api.ACCR_SYNC)
     assert int(s.item()) == int(oracle.reduce(x, "add", "i64"))
     assert int(m.item()) == int(oracle.reduce(x, "max", "i32"))
+
+
+def test_f64_sum_wide_dynamic_range():
+    g = np.random.default_rng(77)
+    for n in [8, 9, 17, 4096, (1 << 20) + 3]:
+        x = np.ldexp(g.standard_normal(n), g.integers(-300, 300, size=n))
+        x[:: 97] = 0.0
+        got = gpu_reduce(x, "add", "f64")
+        truth = oracle.truth_sum(x)
+        assert abs(float(got) - truth) <= 1e-14 * oracle.truth_abs_sum(x), n
+        tiny = np.ldexp(g.standard_normal(n), -1040)          # subnormal range
+        assert abs(float(gpu_reduce(tiny, "add", "f64")) - oracle.truth_sum(tiny)) <= \
+            1e-14 * oracle.truth_abs_sum(tiny) + 5e-324 * n
+
+
+@pytest.mark.slow
+def test_full_size_all_operators():
+    """The all-operator workload at n = 2^28, the inputs bench.py times."""
+    n = 1 << 28
+    xi = inputs.full_range_i32(n, salt=0)
+    xf = inputs.normal(n, np.float32, salt=1000)
+    xd = inputs.normal(n, np.float64, salt=2000)
+    ti = torch.from_numpy(xi).cuda()
+    for op, acc in [("add", "i64"), ("mul", "i32"), ("max", "i32"), ("min", "i32"), ("band", "i32"),
+                    ("bor", "i32"), ("bxor", "i32"), ("land", "i32"), ("lor", "i32")]:
+        out = torch.empty(1, dtype=TD[acc], device="cuda")
+        api.accr_reduce(ti, [api.clause(op, out)])
+        assert out.item() == oracle.reduce(xi, op, acc), op
+    # the adversarial variants keep *, &, && and || informative at full size
+    for op in ["mul", "band", "land", "lor", "max", "min"]:
+        xa = inputs.adversarial_i32(n, op)
+        out = torch.empty(1, dtype=torch.int32, device="cuda")
+        api.accr_reduce(torch.from_numpy(xa).cuda(), [api.clause(op, out)])
+        assert out.item() == oracle.reduce(xa, op, "i32"), op
+    del ti
+    tf = torch.from_numpy(xf).cuda()
+    for op in ["max", "min"]:
+        out = torch.empty(1, dtype=torch.float32, device="cuda")
+        api.accr_reduce(tf, [api.clause(op, out)])
+        assert out.item() == float(oracle.reduce(xf, op)), op
+    for flags, tol in [(0, TOL_F32), (api.ACCR_COMPENSATED, TOL_F32_COMP)]:
+        out = torch.empty(1, dtype=torch.float32, device="cuda")
+        api.accr_reduce(tf, [api.clause("add", out)], flags=flags)
+        assert_sum_close(out.item(), xf, tol)
+    del tf
+    td = torch.from_numpy(xd).cuda()
+    for op in ["max", "min"]:
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        api.accr_reduce(td, [api.clause(op, out)])
+        assert out.item() == float(oracle.reduce(xd, op)), op
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    api.accr_reduce(td, [api.clause("add", out)])
+    assert_sum_close(out.item(), xd, TOL_F64)
