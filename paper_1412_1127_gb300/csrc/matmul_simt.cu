@@ -7,10 +7,11 @@
 // reads a and b straight from global memory; Sec. 4.2 (Matrix Mul) notes that
 // the tiled CUDA SDK version, which stages tiles in shared memory and shares
 // them among a block's threads, is much faster.  This kernel is the tiled
-// form: a CTA computes a 128 x 128 block of c, stages 8-wide k slices of a
+// form: a CTA computes a 128 x 128 block of c, stages 16-wide k slices of a
 // (transposed) and b in double-buffered shared memory, and every thread keeps
 // an 8 x 8 register block (two 4 x 4 quadrants 64 apart, so the 16-byte
-// shared-memory reads of a warp hit distinct banks or broadcast).
+// shared-memory reads of a warp hit distinct banks or broadcast), with its
+// operand fragments double-buffered in registers.
 //
 // Every output still sums its l terms in order 0..LEN-1.  Mode SERIAL rounds
 // each product and then each sum (no fused multiply-add), which is exactly
@@ -22,9 +23,9 @@
 
 namespace accr {
 
-constexpr int MT = 128;  // CTA tile (rows and columns of c)
-constexpr int KT = 8;    // k slice per stage
-constexpr int NTH = 256; // threads per CTA
+constexpr int MT = 128;   // CTA tile (rows and columns of c)
+constexpr int KT = 16;    // k slice per stage
+constexpr int NTH = 256;  // threads per CTA
 
 template <bool SERIAL>
 __device__ __forceinline__ float mac(float acc, float x, float y) {
@@ -41,13 +42,13 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
     const int tx = tid & 15, ty = tid >> 4;
     const int64_t row0 = (int64_t)blockIdx.y * MT, col0 = (int64_t)blockIdx.x * MT;
 
-    // loaders: a 128x8 slice = 256 float4 (one per thread: row tid>>1, k (tid&1)*4);
-    //          b 8x128 slice = 256 float4 (k tid>>5, col (tid&31)*4)
-    const int a_r = tid >> 1, a_k = (tid & 1) * 4;
+    // loaders: a 128x16 slice = 512 float4 (two per thread: rows tid>>2 and 64 + tid>>2,
+    //          k (tid&3)*4); b 16x128 slice = 512 float4 (k tid>>5 and 8 + tid>>5, col (tid&31)*4)
+    const int a_r = tid >> 2, a_k = (tid & 3) * 4;
     const int b_k = tid >> 5, b_c = (tid & 31) * 4;
 
-    auto load_a = [&](int64_t k0, float4 &v) {
-        const int64_t r = row0 + a_r, k = k0 + a_k;
+    auto load_a = [&](int64_t k0, int half, float4 &v) {
+        const int64_t r = row0 + a_r + half * 64, k = k0 + a_k;
         if (VEC && r < len && k + 3 < len) {
             v = __ldg(reinterpret_cast<const float4 *>(a + r * len + k));
         } else {
@@ -57,8 +58,8 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
             v.w = (r < len && k + 3 < len) ? a[r * len + k + 3] : 0.f;
         }
     };
-    auto load_b = [&](int64_t k0, float4 &v) {
-        const int64_t k = k0 + b_k, cc = col0 + b_c;
+    auto load_b = [&](int64_t k0, int half, float4 &v) {
+        const int64_t k = k0 + b_k + half * 8, cc = col0 + b_c;
         if (VEC && k < len && cc + 3 < len) {
             v = __ldg(reinterpret_cast<const float4 *>(b + k * len + cc));
         } else {
@@ -68,12 +69,15 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
             v.w = (k < len && cc + 3 < len) ? b[k * len + cc + 3] : 0.f;
         }
     };
-    auto store_tiles = [&](int buf, const float4 &va, const float4 &vb) {
-        As[buf][a_k + 0][a_r] = va.x;
-        As[buf][a_k + 1][a_r] = va.y;
-        As[buf][a_k + 2][a_r] = va.z;
-        As[buf][a_k + 3][a_r] = va.w;
-        *reinterpret_cast<float4 *>(&Bs[buf][b_k][b_c]) = vb;
+    auto store_tiles = [&](int buf, const float4 (&va)[2], const float4 (&vb)[2]) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            As[buf][a_k + 0][a_r + h * 64] = va[h].x;
+            As[buf][a_k + 1][a_r + h * 64] = va[h].y;
+            As[buf][a_k + 2][a_r + h * 64] = va[h].z;
+            As[buf][a_k + 3][a_r + h * 64] = va[h].w;
+            *reinterpret_cast<float4 *>(&Bs[buf][b_k + h * 8][b_c]) = vb[h];
+        }
     };
 
     float acc[8][8];
@@ -82,9 +86,12 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-    float4 va, vb;
-    load_a(0, va);
-    load_b(0, vb);
+    float4 va[2], vb[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        load_a(0, h, va[h]);
+        load_b(0, h, vb[h]);
+    }
     store_tiles(0, va, vb);
     __syncthreads();
     const int64_t nk = (len + KT - 1) / KT;
@@ -92,17 +99,32 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
         const int cur = (int)(kt & 1);
         const bool more = kt + 1 < nk;
         if (more) {  // fetch the next slice while this one is used
-            load_a((kt + 1) * KT, va);
-            load_b((kt + 1) * KT, vb);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                load_a((kt + 1) * KT, h, va[h]);
+                load_b((kt + 1) * KT, h, vb[h]);
+            }
         }
+        // operand fragments double-buffered in registers: k+1 is read from
+        // shared memory while the 64 products of k issue
+        float4 fa[2][2], fb[2][2];
+        fa[0][0] = *reinterpret_cast<const float4 *>(&As[cur][0][ty * 4]);
+        fa[0][1] = *reinterpret_cast<const float4 *>(&As[cur][0][64 + ty * 4]);
+        fb[0][0] = *reinterpret_cast<const float4 *>(&Bs[cur][0][tx * 4]);
+        fb[0][1] = *reinterpret_cast<const float4 *>(&Bs[cur][0][64 + tx * 4]);
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[cur][k][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[cur][k][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[cur][k][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[cur][k][64 + tx * 4]);
-            const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const int p = k & 1;
+            if (k + 1 < KT) {
+                fa[p ^ 1][0] = *reinterpret_cast<const float4 *>(&As[cur][k + 1][ty * 4]);
+                fa[p ^ 1][1] = *reinterpret_cast<const float4 *>(&As[cur][k + 1][64 + ty * 4]);
+                fb[p ^ 1][0] = *reinterpret_cast<const float4 *>(&Bs[cur][k + 1][tx * 4]);
+                fb[p ^ 1][1] = *reinterpret_cast<const float4 *>(&Bs[cur][k + 1][64 + tx * 4]);
+            }
+            const float ar[8] = {fa[p][0].x, fa[p][0].y, fa[p][0].z, fa[p][0].w,
+                                 fa[p][1].x, fa[p][1].y, fa[p][1].z, fa[p][1].w};
+            const float br[8] = {fb[p][0].x, fb[p][0].y, fb[p][0].z, fb[p][0].w,
+                                 fb[p][1].x, fb[p][1].y, fb[p][1].z, fb[p][1].w};
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
