@@ -301,6 +301,9 @@ def run_scalar(args):
                      for i in range(R)]
     ms_step = ms / args.steps
     value = whole_job_rate(bytes_step, world, ms_step * 1e-3) / 1e9
+    step_ms = [sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for i in range(R)) for k in range(args.steps)]
+    step_gbs = [bytes_step / (t * 1e-3) / 1e9 for t in step_ms]
+    hmean_gbs = len(step_gbs) / sum(1.0 / g for g in step_gbs)
 
     # results of the last step, checked against the oracle on a cheap subset
     peaks, peak_kind = measured_peaks()
@@ -370,6 +373,8 @@ def run_scalar(args):
         autotune.load()
         extra["batched"] = measure_batched(dev, max(3, min(args.steps, 10)), 3)
         torch.cuda.empty_cache()
+        extra["batched_2e8_variant"] = measure_batched(dev, max(3, min(args.steps, 10)), 3, hi=1 << 17)
+        torch.cuda.empty_cache()
         extra["served"] = measure_served(dev, args.served_seconds, args.rate)
         torch.cuda.empty_cache()
         extra["matmul"] = measure_matmul(dev)
@@ -399,6 +404,9 @@ def run_scalar(args):
                        "l2": "inputs larger than L2 (1-2 GiB per region vs 129 MB); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "frac_of_hbm": round(value / world / hbm, 4),
+            "kernel_gbs_per_step": {"harmonic_mean": round(hmean_gbs, 1),
+                                    "median": round(float(np.median(step_gbs)), 1),
+                                    "min": round(min(step_gbs), 1), "max": round(max(step_gbs), 1)},
             "roofline": {"bound": "hbm", "kernel": "reduce_kernel", "achieved": round(achieved, 2),
                          "peak": hbm, "peak_kind": peak_kind + " (copy, hbm_gbs)", "unit": "GB/s",
                          "frac": round(achieved / hbm, 4),
@@ -419,13 +427,13 @@ def run_scalar(args):
     return 0
 
 
-def build_batched(dev, count=20000):
+def build_batched(dev, count=20000, hi=1 << 20):
     """The many-regions workload on the device: 20,000 regions of log-uniform
     length on [1, 2^20]; even ones float N(0,1) with compensated +, odd ones
     int64 with + and ^ (two clauses, one pass)."""
     import torch
     from paper_1412_1127_gb300 import api, inputs
-    lengths, pf, off_f, pi, off_i = inputs.batched_regions(count)
+    lengths, pf, off_f, pi, off_i = inputs.batched_regions(count, hi=hi)
     tf, ti = torch.from_numpy(pf).to(dev), torch.from_numpy(pi).to(dev)
     nf, ni = len(off_f) - 1, len(off_i) - 1
     sf = torch.empty(nf, dtype=torch.float32, device=dev)
@@ -443,12 +451,12 @@ def build_batched(dev, count=20000):
     return regions, nbytes, (sf, si, xi), (pf, off_f, pi, off_i)
 
 
-def measure_batched(dev, steps, warmup, count=20000, tune=False):
+def measure_batched(dev, steps, warmup, count=20000, tune=False, hi=1 << 20):
     """regions/s and GB/s of the prepared (graph) batch, the one-shot batch and
     the plain one-launch-per-region form, on the same regions."""
     import torch
     from paper_1412_1127_gb300 import api
-    regions, nbytes, outs, host = build_batched(dev, count)
+    regions, nbytes, outs, host = build_batched(dev, count, hi)
     R = len(regions)
     tuned = None
     if tune:
@@ -485,9 +493,9 @@ def measure_batched(dev, steps, warmup, count=20000, tune=False):
            / res_plain[0].double().abs().clamp_min(1e-3)).max().item()
     b.destroy()
     return {
-        "workload": "20,000 regions, lengths log-uniform [1, 2^20]: float N(0,1) compensated + / "
+        "workload": "%d regions, lengths log-uniform [1, 2^%d]: float N(0,1) compensated + / "
                     "int64 + and ^ (alternating), %d elements, %.2f GB" % (
-                        int(host[1][-1] + host[3][-1]), nbytes / 1e9),
+                        R, int(math.log2(hi)), int(host[1][-1] + host[3][-1]), nbytes / 1e9),
         "regions": R,
         "batched_graph": {"ms": round(ms_graph, 4), "regions_per_s": round(R / (ms_graph * 1e-3), 1),
                           "gbs": round(nbytes / (ms_graph * 1e-3) / 1e9, 1), "launches": lg},
@@ -507,18 +515,24 @@ SERVED_CLAUSES = {"f32": [("add", "f32")], "i32": [("add", "i64"), ("max", "i32"
                   "i64": [("add", "i64"), ("bxor", "i64")]}
 
 
-def build_served(dev, count, rate, seed=5):
-    """The served workload: Poisson arrivals at `rate` regions/s; each region
-    is float32 (compensated +), int32 (+ into int64 and max) or int64 (+ and ^)
-    with length log-uniform on [2^8, 2^26], at a random offset of a resident
-    pool of its type (2^29 float32, 2^29 int32, 2^28 int64: 6 GiB)."""
+def served_pools(dev, seed=5):
+    """Resident pools of the served workload (2^29 float32, 2^29 int32, 2^28
+    int64: 6 GiB)."""
     import torch
-    from paper_1412_1127_gb300 import api, inputs
+    from paper_1412_1127_gb300 import inputs
     sizes = {"f32": 1 << 29, "i32": 1 << 29, "i64": 1 << 28}
     host = {"f32": inputs.normal(sizes["f32"], np.float32, seed=seed, salt=1),
             "i32": inputs.full_range_i32(sizes["i32"], seed=seed, salt=2),
             "i64": inputs.uniform_i64(sizes["i64"], -(1 << 40), 1 << 40, seed=seed, salt=3)}
-    pools = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    return {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+
+
+def served_requests(dev, pools, count, rate, seed=5):
+    """Poisson arrivals at `rate` regions/s; each region is float32
+    (compensated +), int32 (+ into int64 and max) or int64 (+ and ^) with
+    length log-uniform on [2^8, 2^26], at a random offset of its pool."""
+    import torch
+    from paper_1412_1127_gb300 import api, inputs
     g = inputs.rng(seed, 9)
     lengths = inputs.log_uniform_lengths(count, 1 << 8, 1 << 26, seed=seed, salt=4)
     kinds = g.integers(0, 3, size=count)
@@ -529,12 +543,18 @@ def build_served(dev, count, rate, seed=5):
     for k in range(count):
         t = ["f32", "i32", "i64"][int(kinds[k])]
         n = int(lengths[k])
-        off = int(g.integers(0, sizes[t] - n))
+        off = int(g.integers(0, pools[t].numel() - n))
         regions.append((pools[t][off:off + n], proto[t], api.ACCR_COMPENSATED if t == "f32" else 0))
         nbytes += n * (8 if t == "i64" else 4)
         meta.append((t, off, n))
     arrivals = inputs.poisson_arrivals(rate, count, seed=seed, salt=5)
-    return regions, arrivals, nbytes, meta, host, pools
+    return regions, arrivals, nbytes, meta
+
+
+def build_served(dev, count, rate, seed=5):
+    pools = served_pools(dev, seed)
+    regions, arrivals, nbytes, meta = served_requests(dev, pools, count, rate, seed)
+    return regions, arrivals, nbytes, meta, None, pools
 
 
 def latency_stats(res, n):
@@ -578,10 +598,35 @@ def measure_served(dev, seconds=2.0, rate=50000.0):
             "int_results_equal_plain": bool(same)}
 
 
+def served_sweep(dev, rates, seconds=1.0):
+    """Offered load from the nominal rate up to saturation: served regions/s
+    and p50/p99 latency of the server alone (same region mix)."""
+    from paper_1412_1127_gb300 import api
+    pools = served_pools(dev, seed=6)
+    out = []
+    for rate in rates:
+        count = int(seconds * rate)
+        regions, arrivals, nbytes, meta = served_requests(dev, pools, count, rate, seed=6)
+        srv = api.Server(64 << 30, nstreams=4, max_batch=4096)
+        warm = min(2000, count)
+        srv.replay(regions[:warm], arrivals[:warm])
+        res = srv.replay(regions, arrivals)
+        srv.destroy()
+        st = latency_stats(res, count)
+        st.update({"offered_regions_per_s": rate, "offered_gbs": round(nbytes / arrivals[-1] / 1e9, 1)})
+        out.append(st)
+    del pools
+    return out
+
+
 def run_served(args):
     import torch
     torch.cuda.set_device(0)
-    print(json.dumps(measure_served(torch.device("cuda", 0), args.served_seconds, args.rate)), flush=True)
+    dev = torch.device("cuda", 0)
+    r = measure_served(dev, args.served_seconds, args.rate)
+    if args.sweep:
+        r["rate_sweep"] = served_sweep(dev, [50000, 100000, 150000, 200000, 300000])
+    print(json.dumps(r), flush=True)
     return 0
 
 
@@ -625,6 +670,19 @@ def measure_matmul(dev, length=4096, reps=5):
             r["tensor_tflops"] = round(3 * flops / (ms * 1e-3) / 1e12, 2)
             r["frac_of_bf16_peak"] = round(3 * flops / (ms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]), 4)
             r["note"] = "time includes the two split kernels; tensor work is 3 products"
+            # repeated nest with unchanged operands: the split is reused, so this is the GEMM alone
+            fl = api.ACCR_MM_REUSE_SPLIT
+            api.accr_matmul_nest(at, bt, ct, mode=mode, flags=fl, stream=stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                api.accr_matmul_nest(at, bt, ct, mode=mode, flags=fl, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gms = e0.elapsed_time(e1) / reps
+            r["reuse_split_ms"] = round(gms, 4)
+            r["reuse_split_tensor_tflops"] = round(3 * flops / (gms * 1e-3) / 1e12, 2)
+            r["reuse_split_frac_of_bf16_peak"] = round(3 * flops / (gms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]), 4)
         out[mode] = r
     return out
 
@@ -795,6 +853,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--regions", type=int, default=20000, help="regions of the batched workload")
     ap.add_argument("--tune", action="store_true", help="batched: autotune the split first")
+    ap.add_argument("--sweep", action="store_true", help="served: sweep the offered rate to saturation")
     ap.add_argument("--n", type=int, default=N_SCALAR,
                     help="elements per region (default 2^28; smaller only for profiling captures)")
     args = ap.parse_args()

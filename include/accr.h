@@ -158,6 +158,7 @@ ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t l
 #define ACCR_MM_SIMT_SERIAL 1 /* FP32 on CUDA cores, each product rounded then
                                  added, l in order: the serial program's bits */
 #define ACCR_MM_BF16X3 2      /* tensor cores (tcgen05), BF16x3 split precision */
+#define ACCR_MM_REUSE_SPLIT 0x20u /* flag: reuse the previous call's bf16 split */
 
 /*
  * accr_matmul_nest -- Listing 1a (Sec. 1.3):
@@ -179,7 +180,10 @@ ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t l
  *                 residuals).  Uses library scratch of 8 * len * ceil64(len)
  *                 bytes per stream for the split operands.
  *   flags     ACCR_SYNC (with ACCR_MM_BF16X3 also reports ACCR_ETIMEDOUT if
- *             a pipeline wait inside the kernel ran out)
+ *             a pipeline wait inside the kernel ran out) | ACCR_MM_REUSE_SPLIT
+ *             (ACCR_MM_BF16X3: a and b are unchanged since the previous call
+ *             on this stream with the same a, b and len, so their bf16 split
+ *             is reused instead of recomputed; the caller guarantees it)
  */
 ACCR_API int accr_matmul_nest(const float *a, const float *b, float *c,
                               int64_t len, int32_t mode, uint32_t flags,

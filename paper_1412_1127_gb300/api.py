@@ -293,6 +293,7 @@ def accr_server_replay(server, regions, arrival_s, plain=False, stream=None):
 
 
 ACCR_MM_SIMT, ACCR_MM_SIMT_SERIAL, ACCR_MM_BF16X3 = 0, 1, 2
+ACCR_MM_REUSE_SPLIT = 0x20
 MM_MODES = {"simt": ACCR_MM_SIMT, "serial": ACCR_MM_SIMT_SERIAL, "bf16x3": ACCR_MM_BF16X3}
 
 

@@ -152,12 +152,12 @@ __host__ __device__ __forceinline__ double hd_dmul(double a, double b) {
 // Order-preserving keys: signed integer compare of keys equals the numeric
 // order of the floats, with -0 < +0 (NaN excluded).  The map is an involution.
 __host__ __device__ __forceinline__ int32_t fkey32(uint32_t b) {
-    int32_t s = (int32_t)b;
-    return s >= 0 ? s : (s ^ 0x7fffffff);
+    const int32_t s = (int32_t)b;
+    return s ^ (int32_t)((uint32_t)(s >> 31) >> 1);  // negative: flip all but the sign bit
 }
 __host__ __device__ __forceinline__ int64_t fkey64(uint64_t b) {
-    int64_t s = (int64_t)b;
-    return s >= 0 ? s : (s ^ 0x7fffffffffffffffLL);
+    const int64_t s = (int64_t)b;
+    return s ^ (int64_t)((uint64_t)(s >> 63) >> 1);
 }
 
 template <typename T>

@@ -415,11 +415,13 @@ static int make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t Kp, 
 struct SplitBufs {
     void *buf = nullptr;
     size_t bytes = 0;
+    const float *a = nullptr, *b = nullptr;  // operands of the last split on this stream
+    int64_t len = -1;
 };
 static std::mutex g_split_mu;
 static std::map<std::pair<int, uintptr_t>, SplitBufs> g_split;
 
-int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStream_t s, bool sync) {
+int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStream_t s, bool sync, bool reuse) {
     if (len == 0) return ACCR_OK;
     if (len > (1 << 20)) return set_error(ACCR_EINVAL, "accr_matmul_nest: len too large for the tensor-core path");
     const int64_t M = len, N = len, K = len;
@@ -441,6 +443,8 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
                 sb->buf = nullptr;
                 sb->bytes = 0;
             }
+            sb->a = sb->b = nullptr;
+            sb->len = -1;
             if (cudaMalloc(&sb->buf, need) != cudaSuccess) {
                 cudaGetLastError();
                 return set_error(ACCR_ENOMEM, "accr_matmul_nest: split buffers (%zu bytes)", need);
@@ -457,21 +461,33 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_matmul_nest: clear flag");
     if (rc != ACCR_OK) return rc;
     const DeviceInfo &di = device_info();
-    split_rows_kernel<<<di.sms * 8, 256, 0, s>>>(a, M, K, Kp, ah, al);
-    if ((rc = launched("split_rows_kernel")) != ACCR_OK) return rc;
-    dim3 tg((unsigned)((N + 63) / 64), (unsigned)((Kp + 63) / 64));
-    split_cols_kernel<<<tg, 256, 0, s>>>(b, K, N, Kp, bh, bl);
-    if ((rc = launched("split_cols_kernel")) != ACCR_OK) return rc;
+    if (!(reuse && sb->a == a && sb->b == b && sb->len == len)) {
+        split_rows_kernel<<<di.sms * 8, 256, 0, s>>>(a, M, K, Kp, ah, al);
+        if ((rc = launched("split_rows_kernel")) != ACCR_OK) return rc;
+        dim3 tg((unsigned)((N + 63) / 64), (unsigned)((Kp + 63) / 64));
+        split_cols_kernel<<<tg, 256, 0, s>>>(b, K, N, Kp, bh, bl);
+        if ((rc = launched("split_cols_kernel")) != ACCR_OK) return rc;
+        sb->a = a;
+        sb->b = b;
+        sb->len = len;
+    }
     CUtensorMap mah, mal, mbh, mbl;
     if ((rc = make_map(&mah, ah, M, Kp, TBM)) != ACCR_OK) return rc;
     if ((rc = make_map(&mal, al, M, Kp, TBM)) != ACCR_OK) return rc;
     if ((rc = make_map(&mbh, bh, N, Kp, TBN)) != ACCR_OK) return rc;
     if ((rc = make_map(&mbl, bl, N, Kp, TBN)) != ACCR_OK) return rc;
     const int smem = TSTAGES * STAGE_BYTES + (int)sizeof(TcBars) + 1024;
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [smem] {
-        cudaFuncSetAttribute(bf16x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    });
+    {  // the shared-memory opt-in is a per-device function attribute
+        static std::mutex attr_mu;
+        static bool attr_set[64] = {false};
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (!attr_set[di.id & 63]) {
+            rc = cuda_check(cudaFuncSetAttribute(bf16x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                            "accr_matmul_nest: shared memory opt-in");
+            if (rc != ACCR_OK) return rc;
+            attr_set[di.id & 63] = true;
+        }
+    }
     const int tiles_n = (int)((N + TBN - 1) / TBN), ntiles = tiles_n * (int)((M + TBM - 1) / TBM);
     const int grid = ntiles < di.sms ? ntiles : di.sms;  // persistent: one CTA per SM
     bf16x3_gemm_kernel<<<grid, GEMM_THREADS, smem, s>>>(mah, mal, mbh, mbl, c, (int)M, (int)N, (int)Kp, tiles_n,

@@ -197,9 +197,12 @@ __device__ __noinline__ Thr warp_insert_slow(float *LD, int64_t *LI, float d, in
     return t;
 }
 
+// The hot path is one compare: d <= the warp's k-th distance admits a
+// superset of the winners (ties included); the slow path applies the exact
+// (distance, index) order.
 template <int KT>
 __device__ __forceinline__ void warp_offer(float *LD, int64_t *LI, Thr &thr, float d, int64_t i) {
-    const unsigned mask = __ballot_sync(0xffffffffu, pless(d, i, thr.d, thr.i));
+    const unsigned mask = __ballot_sync(0xffffffffu, d <= thr.d);
     if (mask) thr = warp_insert_slow<KT>(LD, LI, d, i, mask);
 }
 
@@ -233,7 +236,7 @@ __device__ __forceinline__ void cta_merge_warp_lists(float (&D)[KT], int64_t (&I
 }
 
 template <int KT, int NT>
-__global__ void __launch_bounds__(NT) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
+__global__ void __launch_bounds__(NT, (KT <= 8 ? 4 : 2)) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
                                                      int k, int64_t *idx_out, float *d_out, PairSlot *partials,
                                                      unsigned *counter) {
     __shared__ float wld[NT / 32][KT];
@@ -282,11 +285,12 @@ __global__ void __launch_bounds__(NT) nearest_kernel(const float *__restrict__ p
 #pragma unroll
         for (int u = 0; u < NU; ++u) q[u] = qn[u];
         if (vb + vstep < npairs) load(vb + vstep, qn);
+        const int64_t ibase = head + 2 * (vb + lane);  // index of this lane's first point this round
+        const bool full = vb + (NU - 1) * NT + 31 < npairs;
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
-            const int64_t vv = vb + lane + u * NT;
-            const bool ok = vv < npairs;
-            const int64_t i0 = head + 2 * vv;
+            const bool ok = full || (vb + lane + u * NT < npairs);
+            const int64_t i0 = ibase + 2 * u * NT;
             warp_offer<KT>(LD, LI, thr, ok ? sqdist(q[u].x, q[u].y, qx, qy) : INFINITY, ok ? i0 : INT64_MAX);
             warp_offer<KT>(LD, LI, thr, ok ? sqdist(q[u].z, q[u].w, qx, qy) : INFINITY, ok ? i0 + 1 : INT64_MAX);
         }

@@ -89,3 +89,20 @@ def test_rejects_bad_arguments():
     with pytest.raises(api._native.AccrError):
         api.accr_matmul_nest(x, x, x, mode=7)
     assert api.lib().accr_matmul_nest(None, None, None, -1, 0, 0, None) == api._native.ACCR_EINVAL
+
+
+def test_reuse_split_flag():
+    n = 300
+    a = inputs.uniform_matrix(n, n, salt=51)
+    b = inputs.uniform_matrix(n, n, salt=52)
+    at, bt = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    c1, c2 = torch.empty_like(at), torch.empty_like(at)
+    api.accr_matmul_nest(at, bt, c1, mode="bf16x3", flags=api.ACCR_SYNC)
+    api.accr_matmul_nest(at, bt, c2, mode="bf16x3", flags=api.ACCR_SYNC | api.ACCR_MM_REUSE_SPLIT)
+    assert torch.equal(c1, c2)
+    # different operands: the flag does not reuse a stale split
+    b2 = inputs.uniform_matrix(n, n, salt=53)
+    bt2 = torch.from_numpy(b2).cuda()
+    api.accr_matmul_nest(at, bt2, c2, mode="bf16x3", flags=api.ACCR_SYNC | api.ACCR_MM_REUSE_SPLIT)
+    t, s = oracle.matmul_truth(a, b2)
+    assert np.max(np.abs(c2.cpu().numpy() - t) / s) <= 1e-4
