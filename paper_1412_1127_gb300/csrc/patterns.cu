@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(NT, (KT <= 8 ? 4 : 2)) nearest_kernel(const fl
         }
     };
     float4 qn[NU];
-    load(base0, qn);  // software pipeline: the next vectors are in flight while these are offered
+    load(base0, qn);  // software pipeline: the next vectors are in flight while these are tested
     for (int64_t vb = base0; vb < npairs; vb += vstep) {
         float4 q[NU];
 #pragma unroll
@@ -287,12 +287,26 @@ __global__ void __launch_bounds__(NT, (KT <= 8 ? 4 : 2)) nearest_kernel(const fl
         if (vb + vstep < npairs) load(vb + vstep, qn);
         const int64_t ibase = head + 2 * (vb + lane);  // index of this lane's first point this round
         const bool full = vb + (NU - 1) * NT + 31 < npairs;
+        // 2*NU distances, one compare each against the warp's k-th distance;
+        // a single vote per round decides whether any lane has a candidate
+        float d[2 * NU];
+        unsigned cm = 0;
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
             const bool ok = full || (vb + lane + u * NT < npairs);
-            const int64_t i0 = ibase + 2 * u * NT;
-            warp_offer<KT>(LD, LI, thr, ok ? sqdist(q[u].x, q[u].y, qx, qy) : INFINITY, ok ? i0 : INT64_MAX);
-            warp_offer<KT>(LD, LI, thr, ok ? sqdist(q[u].z, q[u].w, qx, qy) : INFINITY, ok ? i0 + 1 : INT64_MAX);
+            d[2 * u] = ok ? sqdist(q[u].x, q[u].y, qx, qy) : INFINITY;
+            d[2 * u + 1] = ok ? sqdist(q[u].z, q[u].w, qx, qy) : INFINITY;
+            cm |= (ok && d[2 * u] <= thr.d ? 1u : 0u) << (2 * u);  // points past the end never compete
+            cm |= (ok && d[2 * u + 1] <= thr.d ? 1u : 0u) << (2 * u + 1);
+        }
+        if (__any_sync(0xffffffffu, cm != 0)) {
+#pragma unroll
+            for (int j = 0; j < 2 * NU; ++j) {
+                const int64_t i = ibase + 2 * (j >> 1) * NT + (j & 1);
+                // the threshold may have dropped since cm was formed: re-test
+                const unsigned mask = __ballot_sync(0xffffffffu, ((cm >> j) & 1u) && d[j] <= thr.d);
+                if (mask) thr = warp_insert_slow<KT>(LD, LI, d[j], i, mask);
+            }
         }
     }
     float D[KT];
