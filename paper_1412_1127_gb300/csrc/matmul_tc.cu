@@ -12,13 +12,16 @@
 // split residuals are of order 2^-16 of |a||b|).
 //
 // Kernel shape: one CTA computes a 128 x 224 block of c with
-// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 224, K = 16).  A TMA
-// producer thread streams 32-wide k slices of the four split operands into a
-// four-stage shared-memory ring (64-byte swizzle, the layout the MMA
-// descriptors expect); an MMA thread waits on each stage's mbarrier, issues
-// the three products for the two 16-wide k steps, and frees the stage with
-// tcgen05.commit; after the last slice the four warps read the accumulator
-// out of tensor memory (tcgen05.ld 32x32b) and store c.
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 224, K = 16).  The split
+// operands are stored packed: every 32-wide k block of a row holds its 32 hi
+// values followed by its 32 lo values, one 128-byte row.  A TMA producer
+// thread streams one such k block of a and of b per stage into a four-stage
+// shared-memory ring (128-byte swizzle, the layout the MMA descriptors
+// expect: two TMA copies and 128-byte rows per stage); an MMA thread waits on
+// each stage's mbarrier, issues the three products for the two 16-wide k
+// steps (hi and lo sit 64 bytes apart inside the swizzled row), and frees the
+// stage with tcgen05.commit; after the last slice the four warps read the
+// accumulator out of tensor memory (tcgen05.ld 32x32b) and store c.
 //
 // Every wait is bounded: if one runs out, the CTA records an error code in
 // global memory, lets its own copies in flight land, releases its tensor
@@ -37,14 +40,16 @@
 namespace accr {
 
 // CTA tile 128 x 224: at LEN 4096 the 19 x 32 = 608 tiles are exactly four
-// waves on 152 SMs (128 x 256 tiles would be 3.4 waves); 32-wide k slices in
-// 64-byte swizzled rows give a four-stage ring in 176 KiB of shared memory.
+// waves on 152 SMs (128 x 256 tiles would be 3.4 waves); 32-wide k slices,
+// hi and lo packed in one 128-byte swizzled row, give a four-stage ring in
+// 176 KiB of shared memory.
 constexpr int TBM = 128, TBN = 224, TBK = 32;
 constexpr int TSTAGES = 4;
-constexpr int SWZ = 64;                                           // swizzle span (bytes) = one k-slice row
-constexpr int A_TILE_BYTES = TBM * TBK * 2;                       // 8 KiB
-constexpr int B_TILE_BYTES = TBN * TBK * 2;                       // 14 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;  // 44 KiB
+constexpr int SWZ = 128;                             // swizzle span (bytes) = one packed k-block row
+constexpr int PK = 2 * TBK;                          // packed row length (bf16): 32 hi then 32 lo
+constexpr int A_TILE_BYTES = TBM * PK * 2;           // 16 KiB
+constexpr int B_TILE_BYTES = TBN * PK * 2;           // 28 KiB
+constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;  // 44 KiB, a multiple of the 1 KiB swizzle pattern
 constexpr int TMEM_COLS = 512;                                    // two accumulators, at columns 0 and 256
 constexpr int GEMM_THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
 constexpr uint32_t kMaxTries = 1u << 24;
@@ -95,15 +100,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row
-// groups 8 x 64 = 512 bytes apart (SBO), descriptor version 1.
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 8 x 128 = 1024 bytes apart (SBO), descriptor version 1.  A start
+// address inside a row (the k step and the hi/lo half, < 128 bytes) leaves
+// the pattern phase, address bits 7-9, at zero.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
     d |= (uint64_t)((8 * SWZ) >> 4) << 32;   // stride byte offset
     d |= (uint64_t)1 << 46;                  // version
-    d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
+    d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
     return d;
 }
 
@@ -141,8 +148,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // two tensor-memory buffers so the epilogue of one tile overlaps the main
 // loop of the next.
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
-    bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                       const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+    bf16x3_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                        float *__restrict__ C, int M, int N, int Kp, int tiles_n, int ntiles, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -192,10 +198,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 uint8_t *st = smem + s * STAGE_BYTES;
                 const uint32_t fb = smem_u32(&bars->full[s]);
                 mbar_expect_tx(fb, STAGE_BYTES);
-                tma_load_2d(smem_u32(st), &tAh, kb * TBK, m0, fb);
-                tma_load_2d(smem_u32(st + A_TILE_BYTES), &tAl, kb * TBK, m0, fb);
-                tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES), &tBh, kb * TBK, n0, fb);
-                tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES + B_TILE_BYTES), &tBl, kb * TBK, n0, fb);
+                tma_load_2d(smem_u32(st), &tA, kb * PK, m0, fb);
+                tma_load_2d(smem_u32(st + A_TILE_BYTES), &tB, kb * PK, n0, fb);
                 issued[s] = use;
             }
         }
@@ -229,11 +233,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t ah = st, al = st + A_TILE_BYTES;
-                const uint32_t bh = st + 2 * A_TILE_BYTES, bl = bh + B_TILE_BYTES;
+                const uint32_t ah = st, al = st + 64;  // hi and lo halves of the packed row
+                const uint32_t bh = st + A_TILE_BYTES, bl = bh + 64;
 #pragma unroll
                 for (int kk = 0; kk < TBK / 16; ++kk) {
-                    const uint32_t off = kk * 32;  // 16 bf16 along K inside the 64-byte swizzle row
+                    const uint32_t off = kk * 32;  // 16 bf16 along K inside each half
                     mma_bf16(acc, smem_desc(ah + off), smem_desc(bh + off), (kb > 0 || kk > 0) ? 1u : 0u);
                     mma_bf16(acc, smem_desc(ah + off), smem_desc(bl + off), 1u);
                     mma_bf16(acc, smem_desc(al + off), smem_desc(bh + off), 1u);
@@ -323,59 +327,98 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// hi = bf16(x), lo = bf16(x - hi); a row-major M x K -> [M][Kp] (zero padded).
-// Each thread splits 8 consecutive elements of a row and stores 16 bytes of
-// hi and of lo.
-__global__ void split_rows_kernel(const float *__restrict__ a, int64_t M, int64_t K, int64_t Kp,
-                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
-    const int64_t k8 = Kp / 8, total = M * k8;
-    const bool vec = (K % 4 == 0) && (((uintptr_t)a & 15) == 0);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / k8, k0 = (t - r * k8) * 8;
-        float x[8];
-        if (vec && k0 + 8 <= K) {
-            const float4 u = __ldg(reinterpret_cast<const float4 *>(a + r * K + k0));
-            const float4 w = __ldg(reinterpret_cast<const float4 *>(a + r * K + k0 + 4));
-            x[0] = u.x, x[1] = u.y, x[2] = u.z, x[3] = u.w, x[4] = w.x, x[5] = w.y, x[6] = w.z, x[7] = w.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = (k0 + e < K) ? a[r * K + k0 + e] : 0.f;
-        }
-        __nv_bfloat16 h[8], l[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) split2(x[e], h[e], l[e]);
-        *reinterpret_cast<uint4 *>(hi + r * Kp + k0) =
-            make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-        *reinterpret_cast<uint4 *>(lo + r * Kp + k0) =
-            make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
-    }
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8]) {
+    return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
 
-// b row-major K x N -> transposed split [N][Kp] (zero padded), 64 x 64 tiles
-// through shared memory; each thread then stores 8 consecutive k of one n.
-__global__ void __launch_bounds__(256) split_cols_kernel(const float *__restrict__ b, int64_t K, int64_t N,
-                                                         int64_t Kp, __nv_bfloat16 *__restrict__ hi,
-                                                         __nv_bfloat16 *__restrict__ lo) {
+// Offset of element k of a packed row: k block k / 32 holds 32 hi values and
+// then 32 lo values, so hi of k sits at 64 (k / 32) + k % 32 and lo 32 later.
+__device__ __forceinline__ int64_t packed_hi(int64_t k) { return (k >> 5) * PK + (k & 31); }
+
+constexpr int SPLIT_THREADS = 256;
+constexpr int SPLIT_A_ITEMS = 4;  // 8-element groups of a per thread
+
+// One launch splits both operands (hi = bf16(x), lo = bf16(x - hi)) into the
+// packed, zero-padded layout the GEMM streams: blocks [0, nblk_a) take a
+// (row-major len x len, rows kept), the rest take 64 x 64 tiles of b
+// (row-major, transposed through shared memory so that a row of the packed
+// b is a column of b).
+__global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(const float *__restrict__ a, const float *__restrict__ b,
+                                                              int64_t len, int64_t Kp, __nv_bfloat16 *__restrict__ ap,
+                                                              __nv_bfloat16 *__restrict__ bp, int nblk_a, int tiles_n,
+                                                              int vec) {
     __shared__ float tile[64][65];
-    const int64_t k0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
-    for (int r = ty; r < 64; r += 4) {
-        const int64_t k = k0 + r, n = n0 + tx;
-        tile[r][tx] = (k < K && n < N) ? __ldg(b + k * N + n) : 0.f;
+    const int64_t row_stride = 2 * Kp;
+    if ((int)blockIdx.x < nblk_a) {
+        const int64_t k8 = Kp / 8, total = len * k8;
+        const int64_t t0 = (int64_t)blockIdx.x * (SPLIT_THREADS * SPLIT_A_ITEMS) + threadIdx.x;
+        float x[SPLIT_A_ITEMS][8];
+#pragma unroll
+        for (int j = 0; j < SPLIT_A_ITEMS; ++j) {  // every load first, then the stores
+            const int64_t t = t0 + (int64_t)j * SPLIT_THREADS;
+            const int64_t r = t / k8, k0 = (t - r * k8) * 8;
+            if (t < total && vec && k0 + 8 <= len) {
+                const float4 u = __ldg(reinterpret_cast<const float4 *>(a + r * len + k0));
+                const float4 w = __ldg(reinterpret_cast<const float4 *>(a + r * len + k0 + 4));
+                x[j][0] = u.x, x[j][1] = u.y, x[j][2] = u.z, x[j][3] = u.w;
+                x[j][4] = w.x, x[j][5] = w.y, x[j][6] = w.z, x[j][7] = w.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[j][e] = (t < total && k0 + e < len) ? a[r * len + k0 + e] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SPLIT_A_ITEMS; ++j) {
+            const int64_t t = t0 + (int64_t)j * SPLIT_THREADS;
+            if (t >= total) break;
+            const int64_t r = t / k8, k0 = (t - r * k8) * 8;
+            __nv_bfloat16 h[8], l[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) split2(x[j][e], h[e], l[e]);
+            __nv_bfloat16 *dst = ap + r * row_stride + packed_hi(k0);
+            *reinterpret_cast<uint4 *>(dst) = pack8(h);
+            *reinterpret_cast<uint4 *>(dst + TBK) = pack8(l);
+        }
+        return;
+    }
+    const int bt = (int)blockIdx.x - nblk_a;
+    const int64_t k0 = (int64_t)(bt / tiles_n) * 64, n0 = (int64_t)(bt % tiles_n) * 64;
+    {  // 64 k x 64 n: 16 float4 per k row, four rows per thread, loads first
+        const int c4 = (threadIdx.x & 15) * 4, r0 = threadIdx.x >> 4;
+        float4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t k = k0 + r0 + 16 * i, n = n0 + c4;
+            if (vec && k < len && n + 4 <= len) {
+                v[i] = __ldg(reinterpret_cast<const float4 *>(b + k * len + n));
+            } else {
+                v[i].x = (k < len && n + 0 < len) ? b[k * len + n + 0] : 0.f;
+                v[i].y = (k < len && n + 1 < len) ? b[k * len + n + 1] : 0.f;
+                v[i].z = (k < len && n + 2 < len) ? b[k * len + n + 2] : 0.f;
+                v[i].w = (k < len && n + 3 < len) ? b[k * len + n + 3] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float *t = &tile[r0 + 16 * i][c4];
+            t[0] = v[i].x, t[1] = v[i].y, t[2] = v[i].z, t[3] = v[i].w;
+        }
     }
     __syncthreads();
-    // 64 n x 8 groups of 8 k = 512 stores of 16 bytes, two per thread
-    for (int g = threadIdx.x; g < 512; g += 256) {
+    // 64 n x 8 groups of 8 k = 512 groups, two per thread; the eight groups of
+    // one n are eight neighbouring threads (256 contiguous output bytes)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int g = threadIdx.x + j * SPLIT_THREADS;
         const int nn = g >> 3, kg = (g & 7) * 8;
         const int64_t n = n0 + nn, k = k0 + kg;
-        if (n >= N || k >= Kp) continue;
+        if (n >= len || k >= Kp) continue;
         __nv_bfloat16 h[8], l[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) split2(tile[kg + e][nn], h[e], l[e]);
-        *reinterpret_cast<uint4 *>(hi + n * Kp + k) =
-            make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-        *reinterpret_cast<uint4 *>(lo + n * Kp + k) =
-            make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+        __nv_bfloat16 *dst = bp + n * row_stride + packed_hi(k);
+        *reinterpret_cast<uint4 *>(dst) = pack8(h);
+        *reinterpret_cast<uint4 *>(dst + TBK) = pack8(l);
     }
 }
 
@@ -397,16 +440,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D bf16 map over [rows][Kp], box {32, box_rows}, 64-byte swizzle.
+// 2-D bf16 map over the packed [rows][2 Kp], box {64, box_rows} (one
+// 128-byte k block per row), 128-byte swizzle.
 static int make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t Kp, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return set_error(ACCR_ECUDA, "accr_matmul_nest: cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * Kp) * 2};
+    cuuint32_t box[2] = {(cuuint32_t)PK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ACCR_ECUDA, "accr_matmul_nest: tensor map encode failed (%d)", (int)r);
     return ACCR_OK;
@@ -426,8 +470,8 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     if (len > (1 << 20)) return set_error(ACCR_EINVAL, "accr_matmul_nest: len too large for the tensor-core path");
     const int64_t M = len, N = len, K = len;
     const int64_t Kp = (K + TBK - 1) / TBK * TBK;
-    const size_t abytes = (size_t)M * Kp * 2, bbytes = (size_t)N * Kp * 2;
-    const size_t need = 2 * abytes + 2 * bbytes + 256;
+    const size_t abytes = (size_t)M * Kp * 4, bbytes = (size_t)N * Kp * 4;  // packed hi + lo
+    const size_t need = abytes + bbytes + 256;
     SplitBufs *sb;
     {
         int dev = 0;
@@ -454,28 +498,28 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     }
     char *base = (char *)sb->buf;
     int *err = (int *)base;
-    __nv_bfloat16 *ah = (__nv_bfloat16 *)(base + 256), *al = (__nv_bfloat16 *)(base + 256 + abytes);
-    __nv_bfloat16 *bh = (__nv_bfloat16 *)(base + 256 + 2 * abytes), *bl = (__nv_bfloat16 *)(base + 256 + 2 * abytes + bbytes);
+    __nv_bfloat16 *ap = (__nv_bfloat16 *)(base + 256), *bp = (__nv_bfloat16 *)(base + 256 + abytes);
     int rc = launch_guard("bf16x3_gemm_kernel");
     if (rc != ACCR_OK) return rc;
     rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_matmul_nest: clear flag");
     if (rc != ACCR_OK) return rc;
     const DeviceInfo &di = device_info();
     if (!(reuse && sb->a == a && sb->b == b && sb->len == len)) {
-        split_rows_kernel<<<di.sms * 8, 256, 0, s>>>(a, M, K, Kp, ah, al);
-        if ((rc = launched("split_rows_kernel")) != ACCR_OK) return rc;
-        dim3 tg((unsigned)((N + 63) / 64), (unsigned)((Kp + 63) / 64));
-        split_cols_kernel<<<tg, 256, 0, s>>>(b, K, N, Kp, bh, bl);
-        if ((rc = launched("split_cols_kernel")) != ACCR_OK) return rc;
+        const int64_t items_a = M * (Kp / 8), per_blk = SPLIT_THREADS * SPLIT_A_ITEMS;
+        const int64_t nblk_a = (items_a + per_blk - 1) / per_blk;
+        const int64_t tn = (N + 63) / 64, nblk_b = tn * ((Kp + 63) / 64);
+        if (nblk_a + nblk_b > INT32_MAX) return set_error(ACCR_EINVAL, "accr_matmul_nest: len too large for the split");
+        const int vec = (K % 4 == 0) && (((uintptr_t)a & 15) == 0) && (((uintptr_t)b & 15) == 0);
+        split_kernel<<<(unsigned)(nblk_a + nblk_b), SPLIT_THREADS, 0, s>>>(a, b, len, Kp, ap, bp, (int)nblk_a,
+                                                                          (int)tn, vec);
+        if ((rc = launched("split_kernel")) != ACCR_OK) return rc;
         sb->a = a;
         sb->b = b;
         sb->len = len;
     }
-    CUtensorMap mah, mal, mbh, mbl;
-    if ((rc = make_map(&mah, ah, M, Kp, TBM)) != ACCR_OK) return rc;
-    if ((rc = make_map(&mal, al, M, Kp, TBM)) != ACCR_OK) return rc;
-    if ((rc = make_map(&mbh, bh, N, Kp, TBN)) != ACCR_OK) return rc;
-    if ((rc = make_map(&mbl, bl, N, Kp, TBN)) != ACCR_OK) return rc;
+    CUtensorMap ma, mb;
+    if ((rc = make_map(&ma, ap, M, Kp, TBM)) != ACCR_OK) return rc;
+    if ((rc = make_map(&mb, bp, N, Kp, TBN)) != ACCR_OK) return rc;
     const int smem = TSTAGES * STAGE_BYTES + (int)sizeof(TcBars) + 1024;
     {  // the shared-memory opt-in is a per-device function attribute
         static std::mutex attr_mu;
@@ -490,7 +534,7 @@ int matmul_bf16x3(const float *a, const float *b, float *c, int64_t len, cudaStr
     }
     const int tiles_n = (int)((N + TBN - 1) / TBN), ntiles = tiles_n * (int)((M + TBM - 1) / TBM);
     const int grid = ntiles < di.sms ? ntiles : di.sms;  // persistent: one CTA per SM
-    bf16x3_gemm_kernel<<<grid, GEMM_THREADS, smem, s>>>(mah, mal, mbh, mbl, c, (int)M, (int)N, (int)Kp, tiles_n,
+    bf16x3_gemm_kernel<<<grid, GEMM_THREADS, smem, s>>>(ma, mb, c, (int)M, (int)N, (int)Kp, tiles_n,
                                                         ntiles, err);
     if ((rc = launched("bf16x3_gemm_kernel")) != ACCR_OK) return rc;
     if (sync) {
