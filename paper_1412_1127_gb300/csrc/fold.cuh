@@ -336,9 +336,17 @@ __device__ __forceinline__ void fold_vec(int w, Acc &A, const uint4 *v) {
         switch (w) {
         case W_ADDF: {
             if constexpr (F32) {
-                float a = u2f((uint32_t)A.a);
-                for_each_elem<T, NV>(v, [&](T x) { a = a + x; });
-                A.a = f2u(a);
+                // one partial sum per vector slot: dependency chains of NV
+                // adds instead of 4 NV, merged pairwise at the end
+                float p0 = u2f((uint32_t)A.a), p1 = -0.f, p2 = -0.f, p3 = -0.f;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    p0 = p0 + __uint_as_float(v[i].x);
+                    p1 = p1 + __uint_as_float(v[i].y);
+                    p2 = p2 + __uint_as_float(v[i].z);
+                    p3 = p3 + __uint_as_float(v[i].w);
+                }
+                A.a = f2u((p0 + p1) + (p2 + p3));
             } else {
                 A.a = d2u(__dadd_rn(u2d(A.a), chunk_sum_f64<NV>(v)));
             }
@@ -367,13 +375,16 @@ __device__ __forceinline__ void fold_vec(int w, Acc &A, const uint4 *v) {
             A.a = d2u(a);
         } break;
         case W_MAXF: {
-            if constexpr (F32) {
-                int32_t a = (int32_t)(uint32_t)A.a;
-                for_each_elem<T, NV>(v, [&](T x) {
-                    int32_t k = fkey32(__float_as_uint(x));
-                    a = k > a ? k : a;
-                });
-                A.a = (uint32_t)a;
+            if constexpr (F32) {  // four independent key chains, as for the sum
+                int32_t a0 = (int32_t)(uint32_t)A.a, a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    a0 = max(a0, fkey32(v[i].x));
+                    a1 = max(a1, fkey32(v[i].y));
+                    a2 = max(a2, fkey32(v[i].z));
+                    a3 = max(a3, fkey32(v[i].w));
+                }
+                A.a = (uint32_t)max(max(a0, a1), max(a2, a3));
             } else {
                 int64_t a = (int64_t)A.a;
                 for_each_elem<T, NV>(v, [&](T x) {
@@ -385,12 +396,15 @@ __device__ __forceinline__ void fold_vec(int w, Acc &A, const uint4 *v) {
         } break;
         case W_MINF: {
             if constexpr (F32) {
-                int32_t a = (int32_t)(uint32_t)A.a;
-                for_each_elem<T, NV>(v, [&](T x) {
-                    int32_t k = fkey32(__float_as_uint(x));
-                    a = k < a ? k : a;
-                });
-                A.a = (uint32_t)a;
+                int32_t a0 = (int32_t)(uint32_t)A.a, a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    a0 = min(a0, fkey32(v[i].x));
+                    a1 = min(a1, fkey32(v[i].y));
+                    a2 = min(a2, fkey32(v[i].z));
+                    a3 = min(a3, fkey32(v[i].w));
+                }
+                A.a = (uint32_t)min(min(a0, a1), min(a2, a3));
             } else {
                 int64_t a = (int64_t)A.a;
                 for_each_elem<T, NV>(v, [&](T x) {

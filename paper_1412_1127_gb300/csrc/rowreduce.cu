@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fold.cuh"
@@ -34,7 +35,10 @@ __device__ __forceinline__ uint4 ld_row(const uint4 *p) {
     return v;
 }
 
-template <typename T, int NC>
+// W0 / W1 >= 0 fix the working codes of clauses 0 / 1 at compile time (the
+// fold's operator switch then disappears from the row loop); -1 reads them
+// from the arguments.
+template <typename T, int NC, int W0 = -1, int W1 = -1>
 __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ RowArgs p) {
     constexpr bool E64 = sizeof(T) == 8;
     constexpr int EPV = 16 / (int)sizeof(T);
@@ -43,7 +47,7 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
     const int64_t cols = p.cols;
     int w[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) w[c] = p.cl[c].wcode;
+    for (int c = 0; c < NC; ++c) w[c] = (c == 0 && W0 >= 0) ? W0 : (c == 1 && W1 >= 0) ? W1 : p.cl[c].wcode;
 
     for (int64_t r = (int64_t)blockIdx.x * (WB / 32) + (threadIdx.x >> 5); r < p.rows; r += warps) {
         const T *row = (const T *)p.A + r * p.ld;
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
     }
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int W0 = -1, int W1 = -1>
 static int row_grid(int64_t rows) {
     static std::mutex mu;
     static int cached[64] = {0};
@@ -104,7 +108,7 @@ static int row_grid(int64_t rows) {
         int &slot = cached[d.id & 63];
         if (!slot) {
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowreduce_kernel<T, NC>, WB, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowreduce_kernel<T, NC, W0, W1>, WB, 0);
             if (per_sm < 1) per_sm = 1;
             slot = per_sm * d.sms;
         }
@@ -115,16 +119,50 @@ static int row_grid(int64_t rows) {
     return (int)(want < maxg ? want : maxg);
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int W0 = -1, int W1 = -1>
 static int row_launch_t(RowArgs &a, cudaStream_t s) {
     int rc = launch_guard("rowreduce_kernel");
     if (rc != ACCR_OK) return rc;
-    rowreduce_kernel<T, NC><<<row_grid<T, NC>(a.rows), WB, 0, s>>>(a);
+    rowreduce_kernel<T, NC, W0, W1><<<row_grid<T, NC, W0, W1>(a.rows), WB, 0, s>>>(a);
     return launched("rowreduce_kernel");
+}
+
+// A sum together with a max or a min (the two-clause form of a region that
+// reports a total and an extreme) gets a kernel with both codes fixed: the
+// generic two-clause fold needs 64 registers a thread, the fixed one 32-40,
+// which leaves room for more rows in flight per SM.
+template <typename T, int W0, int W1>
+static bool pair_launch(RowArgs &a, cudaStream_t s, int &rc) {
+    if (a.cl[0].wcode != W0 || a.cl[1].wcode != W1) return false;
+    rc = row_launch_t<T, 2, W0, W1>(a, s);
+    return true;
+}
+
+template <typename T>
+static bool row_launch_pair(RowArgs &a, cudaStream_t s, int &rc) {
+    auto is_sum = [](int w) { return w == W_ADD32 || w == W_ADD64 || w == W_ADDF || w == W_ADDF_COMP; };
+    if (!is_sum(a.cl[0].wcode) && is_sum(a.cl[1].wcode)) {  // each clause carries its own output
+        const ClauseDev t = a.cl[0];
+        a.cl[0] = a.cl[1];
+        a.cl[1] = t;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        return pair_launch<T, W_ADDF, W_MAXF>(a, s, rc) || pair_launch<T, W_ADDF, W_MINF>(a, s, rc) ||
+               pair_launch<T, W_ADDF_COMP, W_MAXF>(a, s, rc) || pair_launch<T, W_ADDF_COMP, W_MINF>(a, s, rc);
+    } else if constexpr (std::is_same<T, double>::value) {
+        return pair_launch<T, W_ADDF, W_MAXF>(a, s, rc) || pair_launch<T, W_ADDF, W_MINF>(a, s, rc);
+    } else if constexpr (std::is_same<T, int32_t>::value) {
+        return pair_launch<T, W_ADD32, W_MAXI>(a, s, rc) || pair_launch<T, W_ADD32, W_MINI>(a, s, rc) ||
+               pair_launch<T, W_ADD64, W_MAXI>(a, s, rc) || pair_launch<T, W_ADD64, W_MINI>(a, s, rc);
+    } else {
+        return pair_launch<T, W_ADD64, W_MAXI>(a, s, rc) || pair_launch<T, W_ADD64, W_MINI>(a, s, rc);
+    }
 }
 
 template <typename T>
 static int row_launch(RowArgs &a, cudaStream_t s) {
+    int rc = ACCR_OK;
+    if (a.nc == 2 && row_launch_pair<T>(a, s, rc)) return rc;
     switch (a.nc) {
     case 1: return row_launch_t<T, 1>(a, s);
     case 2: return row_launch_t<T, 2>(a, s);

@@ -72,3 +72,53 @@ def test_two_clauses_rows_full_size():
     for r in idx:
         truth = oracle.truth_sum(A[r])
         assert abs(float(s_np[r]) - truth) / max(abs(truth), 0.1 * 64 * 0.577) <= TOL_F32
+
+
+PAIR_CASES = [  # (element type, sum variable, flags) for the fixed-code two-clause kernels
+    ("i32", "i32", 0), ("i32", "i64", 0), ("i64", "i64", 0),
+    ("f32", "f32", 0), ("f32", "f32", api.ACCR_COMPENSATED), ("f64", "f64", 0)]
+
+
+@pytest.mark.parametrize("t,acc,flags", PAIR_CASES)
+@pytest.mark.parametrize("ext", ["max", "min"])
+@pytest.mark.parametrize("sum_first", [True, False])
+@pytest.mark.parametrize("shape", [(129, 1023), (300, 4096), (3, 70001)])
+def test_sum_and_extreme_pairs(t, acc, flags, ext, sum_first, shape):
+    """A sum and a max/min in one pass, in either clause order: each variable
+    gets its own row fold (integers bit-exact, float extremes bit-exact, float
+    sums within the sum tolerance)."""
+    g = np.random.default_rng(shape[0] + shape[1])
+    if t in ("i32", "i64"):
+        A = g.integers(-(1 << 31), 1 << 31, size=shape, dtype=np.int64).astype(np.int32 if t == "i32" else np.int64)
+    else:
+        A = inputs.uniform_matrix(*shape)
+        A = A.astype(np.float64) if t == "f64" else A
+    At = torch.from_numpy(A).cuda()
+    rows, cols = shape
+    s = torch.full((rows,), 9, dtype=TD[acc], device="cuda")
+    m = torch.full((rows,), 9, dtype=TD[t], device="cuda")
+    cls = [api.clause("add", s), api.clause(ext, m)]
+    api.accr_rowreduce(At, cls if sum_first else cls[::-1], flags=flags)
+    s_np, m_np = s.cpu().numpy(), m.cpu().numpy()
+    want_m = oracle.rowreduce(A, ext, t) if t in ("i32", "i64") else oracle.rowreduce(A, ext)
+    if t in ("i32", "i64"):
+        assert np.array_equal(m_np, want_m)
+        assert np.array_equal(s_np, oracle.rowreduce(A, "add", acc))
+        return
+    assert same_bits(m_np, want_m)
+    tol = TOL_F32_COMP if flags else (TOL_F32 if t == "f32" else 1e-12)
+    for r in range(0, rows, max(1, rows // 40)):
+        truth = oracle.truth_sum(A[r])
+        assert abs(float(s_np[r]) - truth) / max(abs(truth), 0.1 * math.sqrt(cols) * 0.577) <= tol, (r, t)
+
+
+def test_generic_two_clause_rows():
+    """A pair outside the fixed-code set (product and xor) runs the generic fold."""
+    g = np.random.default_rng(5)
+    A = g.integers(-(1 << 31), 1 << 31, size=(77, 3000), dtype=np.int64).astype(np.int32)
+    At = torch.from_numpy(A).cuda()
+    p = torch.empty(77, dtype=torch.int64, device="cuda")
+    x = torch.empty(77, dtype=torch.int32, device="cuda")
+    api.accr_rowreduce(At, [api.clause("mul", p), api.clause("bxor", x)])
+    assert np.array_equal(p.cpu().numpy(), oracle.rowreduce(A, "mul", "i64"))
+    assert np.array_equal(x.cpu().numpy(), oracle.rowreduce(A, "bxor", "i32"))
