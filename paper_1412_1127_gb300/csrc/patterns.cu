@@ -154,6 +154,15 @@ __device__ __forceinline__ void warp_topk(float (&D)[KT], int64_t (&I)[KT], floa
     }
 }
 
+// Streaming 16-byte load of two points (read once: no L1 allocation).
+__device__ __forceinline__ float4 ld_pts(const float4 *p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ float sqdist(float x, float y, float qx, float qy) {
     const float dx = __fsub_rn(x, qx), dy = __fsub_rn(y, qy);
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));  // no fused multiply-add
@@ -206,52 +215,94 @@ __device__ __forceinline__ void warp_offer(float *LD, int64_t *LI, Thr &thr, flo
     if (mask) thr = warp_insert_slow<KT>(LD, LI, d, i, mask);
 }
 
-// Warp 0 merges the CTA's warp lists (shared memory) into the CTA's KT
-// smallest, held in D/I of every lane of warp 0.
+// The CTA's KT smallest of its warps' lists (shared memory), written to
+// MD/MI: each entry's rank is the number of entries before it in the
+// (distance, index) order, equal entries (placeholders) ordered by position,
+// so the ranks are distinct and entry r of the result is the one of rank r.
 template <int KT, int NT>
-__device__ __forceinline__ void cta_merge_warp_lists(float (&D)[KT], int64_t (&I)[KT], float (*wld)[KT],
-                                                     int64_t (*wli)[KT]) {
+__device__ __forceinline__ void cta_merge_warp_lists(const float (*wld)[KT], const int64_t (*wli)[KT], float *MD,
+                                                     int64_t *MI) {
+    constexpr int NC = (NT / 32) * KT;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp == 0) {
-        if (lane < NT / 32) {
-#pragma unroll
-            for (int j = 0; j < KT; ++j) {
-                D[j] = wld[lane][j];
-                I[j] = wli[lane][j];
-            }
-        } else {
-            list_init<KT>(D, I);
+    const float *fd = &wld[0][0];
+    const int64_t *fi = &wli[0][0];
+    for (int c = threadIdx.x; c < NC; c += NT) {
+        const float dc = fd[c];
+        const int64_t ic = fi[c];
+        int rank = 0;
+        for (int o = 0; o < NC; ++o) {
+            const float dd = fd[o];
+            const int64_t io = fi[o];
+            rank += (pless(dd, io, dc, ic) || (dd == dc && io == ic && o < c)) ? 1 : 0;
         }
-        float RD[KT];
-        int64_t RI[KT];
-        warp_topk<KT>(D, I, RD, RI);
-#pragma unroll
-        for (int j = 0; j < KT; ++j) {
-            D[j] = RD[j];
-            I[j] = RI[j];
+        if (rank < KT) {
+            MD[rank] = dc;
+            MI[rank] = ic;
         }
     }
     __syncthreads();
 }
 
+// Last CTA: every thread folds a strided share of the nc partial slots into
+// a list in registers (placeholders skipped), and each warp writes the top KT
+// of its lanes' lists to its shared-memory list.  Out of line, so that its
+// registers do not weigh on the scan loop.
 template <int KT, int NT>
-__global__ void __launch_bounds__(NT, (KT <= 8 ? 4 : 2)) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
+__device__ __noinline__ void final_lists(const PairSlot *partials, int64_t nc, float *LD, int64_t *LI) {
+    const int lane = threadIdx.x & 31;
+    float D[KT];
+    int64_t I[KT];
+    list_init<KT>(D, I);
+    constexpr int B = KT <= 8 ? 8 : 2;  // slots in flight per thread (the lists of 16 need the registers)
+    for (int64_t c0 = threadIdx.x; c0 < nc; c0 += (int64_t)B * NT) {
+        uint4 raw[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int64_t c = c0 + (int64_t)u * NT;
+            raw[u] = c < nc ? __ldcg(reinterpret_cast<const uint4 *>(partials + c)) : make_uint4(~0u, 0x7fffffffu, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int64_t i = (int64_t)(((uint64_t)raw[u].y << 32) | raw[u].x);
+            if (i != INT64_MAX) list_insert<KT>(D, I, __uint_as_float(raw[u].z), i);
+        }
+    }
+    float RD[KT];
+    int64_t RI[KT];
+    warp_topk<KT>(D, I, RD, RI);
+#pragma unroll
+    for (int j = 0; j < KT; ++j)
+        if (j == lane) {
+            LD[j] = RD[j];
+            LI[j] = RI[j];
+        }
+}
+
+// bound (nullable, device): a distance that at least k of the points reach
+// (the k-th smallest distance of a sample of them).  Every list starts as KT
+// placeholders (bound, no index), so only points with d <= bound are ever
+// tested in the slow path; since k real points lie within the bound, the
+// placeholders never reach the output.
+template <int KT, int NT>
+__global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
                                                      int k, int64_t *idx_out, float *d_out, PairSlot *partials,
-                                                     unsigned *counter) {
+                                                     unsigned *counter, const float *bound) {
     __shared__ float wld[NT / 32][KT];
     __shared__ int64_t wli[NT / 32][KT];
+    __shared__ float MD[KT];
+    __shared__ int64_t MI[KT];
     __shared__ int am_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *LD = wld[warp];
     int64_t *LI = wli[warp];
+    const float T = bound ? __ldg(bound) : INFINITY;
     if (lane < KT) {
-        LD[lane] = INFINITY;
+        LD[lane] = T;
         LI[lane] = INT64_MAX;
     }
     __syncwarp();
     Thr thr;
-    thr.d = INFINITY;
+    thr.d = T;
     thr.i = INT64_MAX;
     // points are float2; the vector part starts at a 16-byte boundary
     const int64_t head = (((uintptr_t)pts & 15) != 0 && n > 0) ? 1 : 0;
@@ -266,59 +317,60 @@ __global__ void __launch_bounds__(NT, (KT <= 8 ? 4 : 2)) nearest_kernel(const fl
         if (lane == 1 && last < n) d = sqdist(pts[2 * last], pts[2 * last + 1], qx, qy), i = last;
         warp_offer<KT>(LD, LI, thr, d, i);
     }
-    // NU 16-byte loads (2 points each) in flight per lane per iteration; the
-    // trip count is uniform across each warp so that the ballots see 32 lanes
-    constexpr int NU = 4;
+    // Full rounds: NU 16-byte loads (2 points each) per lane, every one in
+    // range, so no per-point bounds test; the round's smallest distance is
+    // compared once with the warp's k-th, and only a round in which some lane
+    // beats it tests its points one by one.  The trip count is uniform across
+    // each warp so that the votes see 32 lanes.
+    constexpr int NU = 16;
     const int64_t vstep = nth * NU;
-    const int64_t base0 = (int64_t)blockIdx.x * (NT * NU) + warp * 32;
-    auto load = [&](int64_t vb, float4 (&q)[NU]) {
-#pragma unroll
-        for (int u = 0; u < NU; ++u) {
-            const int64_t vv = vb + lane + u * NT;
-            q[u] = vv < npairs ? __ldg(v4 + vv) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    float4 qn[NU];
-    load(base0, qn);  // software pipeline: the next vectors are in flight while these are tested
-    for (int64_t vb = base0; vb < npairs; vb += vstep) {
+    int64_t vb = (int64_t)blockIdx.x * (NT * NU) + warp * 32;
+    for (; vb + (NU - 1) * NT + 31 < npairs; vb += vstep) {
+        const float4 *p = v4 + vb + lane;
         float4 q[NU];
 #pragma unroll
-        for (int u = 0; u < NU; ++u) q[u] = qn[u];
-        if (vb + vstep < npairs) load(vb + vstep, qn);
-        const int64_t ibase = head + 2 * (vb + lane);  // index of this lane's first point this round
-        const bool full = vb + (NU - 1) * NT + 31 < npairs;
-        // 2*NU distances, one compare each against the warp's k-th distance;
-        // a single vote per round decides whether any lane has a candidate
-        float d[2 * NU];
-        unsigned cm = 0;
+        for (int u = 0; u < NU; ++u) q[u] = ld_pts(p + u * NT);
+        float dm = INFINITY;
 #pragma unroll
-        for (int u = 0; u < NU; ++u) {
-            const bool ok = full || (vb + lane + u * NT < npairs);
-            d[2 * u] = ok ? sqdist(q[u].x, q[u].y, qx, qy) : INFINITY;
-            d[2 * u + 1] = ok ? sqdist(q[u].z, q[u].w, qx, qy) : INFINITY;
-            cm |= (ok && d[2 * u] <= thr.d ? 1u : 0u) << (2 * u);  // points past the end never compete
-            cm |= (ok && d[2 * u + 1] <= thr.d ? 1u : 0u) << (2 * u + 1);
-        }
-        if (__any_sync(0xffffffffu, cm != 0)) {
+        for (int u = 0; u < NU; ++u)
+            dm = fminf(dm, fminf(sqdist(q[u].x, q[u].y, qx, qy), sqdist(q[u].z, q[u].w, qx, qy)));
+        if (__any_sync(0xffffffffu, dm <= thr.d)) {
+            // recompute the distances (the same arithmetic) rather than keep
+            // them in registers: the registers go to the loads in flight
+            const int64_t ibase = head + 2 * (vb + lane);  // this lane's first point this round
 #pragma unroll
             for (int j = 0; j < 2 * NU; ++j) {
-                const int64_t i = ibase + 2 * (j >> 1) * NT + (j & 1);
-                // the threshold may have dropped since cm was formed: re-test
-                const unsigned mask = __ballot_sync(0xffffffffu, ((cm >> j) & 1u) && d[j] <= thr.d);
-                if (mask) thr = warp_insert_slow<KT>(LD, LI, d[j], i, mask);
+                const float4 &v = q[j >> 1];
+                const float dj = (j & 1) ? sqdist(v.z, v.w, qx, qy) : sqdist(v.x, v.y, qx, qy);
+                // the threshold may drop between the points: test each again
+                const unsigned mask = __ballot_sync(0xffffffffu, dj <= thr.d);
+                if (mask) thr = warp_insert_slow<KT>(LD, LI, dj, ibase + 2 * (j >> 1) * NT + (j & 1), mask);
             }
         }
     }
-    float D[KT];
-    int64_t I[KT];
-    cta_merge_warp_lists<KT, NT>(D, I, wld, wli);
+    if (vb < npairs) {  // the last, partial round: points past the end never compete
+        const int64_t ibase = head + 2 * (vb + lane);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int64_t vv = vb + lane + u * NT;
+            const bool ok = vv < npairs;
+            const float4 q = ok ? ld_pts(v4 + vv) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float d0 = ok ? sqdist(q.x, q.y, qx, qy) : INFINITY;
+            const float d1 = ok ? sqdist(q.z, q.w, qx, qy) : INFINITY;
+            unsigned mask = __ballot_sync(0xffffffffu, ok && d0 <= thr.d);
+            if (mask) thr = warp_insert_slow<KT>(LD, LI, d0, ibase + 2 * u * NT, mask);
+            mask = __ballot_sync(0xffffffffu, ok && d1 <= thr.d);
+            if (mask) thr = warp_insert_slow<KT>(LD, LI, d1, ibase + 2 * u * NT + 1, mask);
+        }
+    }
+    cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
     const int G = gridDim.x;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int j = 0; j < KT; ++j) {
             PairSlot p;
-            p.i = I[j];
-            p.d = D[j];
+            p.i = MI[j];
+            p.d = MD[j];
             p.pad = 0;
             partials[(int64_t)blockIdx.x * KT + j] = p;
         }
@@ -328,34 +380,100 @@ __global__ void __launch_bounds__(NT, (KT <= 8 ? 4 : 2)) nearest_kernel(const fl
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    if (lane < KT) {
-        LD[lane] = INFINITY;
-        LI[lane] = INT64_MAX;
-    }
-    __syncwarp();
-    thr.d = INFINITY;
-    thr.i = INT64_MAX;
-    const int64_t nc = (int64_t)G * KT;
-    for (int64_t c0 = 0; c0 < nc; c0 += NT) {  // uniform trip count: whole warps take part in the ballots
-        const int64_t c = c0 + threadIdx.x;
-        float d = INFINITY;
-        int64_t i = INT64_MAX;
-        if (c < nc) {
-            const uint4 raw = __ldcg(reinterpret_cast<const uint4 *>(partials + c));
-            i = (int64_t)(((uint64_t)raw.y << 32) | raw.x);
-            d = __uint_as_float(raw.z);
-        }
-        warp_offer<KT>(LD, LI, thr, d, i);
-    }
-    cta_merge_warp_lists<KT, NT>(D, I, wld, wli);
+    final_lists<KT, NT>(partials, (int64_t)G * KT, LD, LI);
+    cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
     if (threadIdx.x == 0) {
         for (int j = 0; j < k; ++j) {
-            const bool real = I[j] != INT64_MAX;
-            idx_out[j] = real ? I[j] : -1;
-            d_out[j] = real ? D[j] : INFINITY;
+            const bool real = MI[j] != INT64_MAX;
+            idx_out[j] = real ? MI[j] : -1;
+            d_out[j] = real ? MD[j] : INFINITY;
         }
         *counter = 0u;
     }
+}
+
+// The bound: each warp of NK_BOUND_CTAS CTAs takes the smallest distance of
+// its share of a sample (NK_CHUNKS chunks of NK_CHUNK consecutive points,
+// spread evenly over the array: chunk c starts at point c * stride); those
+// minima belong to distinct points, so the k-th smallest of them is a
+// distance that at least k points reach.  The last CTA to finish selects it.
+constexpr int NK_CHUNK = 512, NK_CHUNKS = 128, NK_BOUND_CTAS = 64;
+constexpr int NK_BOUND_WARPS = NK_BOUND_CTAS * (NK_THREADS / 32);  // 512 minima
+constexpr int64_t NK_BOUND_MIN_N = 1 << 22;  // smaller inputs skip the bound (its launch costs more)
+constexpr int NK_BOUND_PER_THREAD = NK_CHUNK * (NK_CHUNKS / NK_BOUND_CTAS) / NK_THREADS;
+
+template <int KT>
+__device__ __forceinline__ void flist_insert(float (&D)[KT], float d) {
+    if (!(d < D[KT - 1])) return;  // NaN never enters
+#pragma unroll
+    for (int j = KT - 1; j > 0; --j) D[j] = d < D[j - 1] ? D[j - 1] : (d < D[j] ? d : D[j]);
+    D[0] = d < D[0] ? d : D[0];
+}
+
+template <int KT>
+__global__ void __launch_bounds__(NK_THREADS) nearest_bound_kernel(const float2 *__restrict__ pts, int64_t stride,
+                                                                    float qx, float qy, int k, float *minima,
+                                                                    unsigned *counter, float *bound) {
+    __shared__ int am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 v[NK_BOUND_PER_THREAD];
+#pragma unroll
+    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) {  // every load first
+        const int t = e * NK_THREADS + threadIdx.x;   // point t of this CTA's chunks
+        const int c = blockIdx.x * (NK_CHUNKS / NK_BOUND_CTAS) + t / NK_CHUNK;
+        v[e] = __ldg(pts + (int64_t)c * stride + (t % NK_CHUNK));
+    }
+    float m = INFINITY;  // fminf passes over NaN distances
+#pragma unroll
+    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) m = fminf(m, sqdist(v[e].x, v[e].y, qx, qy));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) minima[blockIdx.x * (NK_THREADS / 32) + warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        am_last = atomicAdd(counter, 1u) == (unsigned)gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!am_last || warp != 0) return;
+    __threadfence();
+    float D[KT];
+#pragma unroll
+    for (int j = 0; j < KT; ++j) D[j] = INFINITY;
+    constexpr int PER_LANE = NK_BOUND_WARPS / 32;
+    float mv[PER_LANE];
+#pragma unroll
+    for (int j = 0; j < PER_LANE; ++j) mv[j] = __ldcg(minima + j * 32 + lane);  // all loads in flight
+#pragma unroll
+    for (int j = 0; j < PER_LANE; ++j) flist_insert<KT>(D, mv[j]);
+    // the k-th smallest of the 32 lanes' ascending lists: k rounds of a warp
+    // minimum, each taking the head of exactly one lane
+    float t = INFINITY;
+    for (int r = 0; r < k; ++r) {
+        float w = D[0];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
+        t = w;
+        const unsigned who = __ballot_sync(0xffffffffu, D[0] == w);
+        if (lane == __ffs(who) - 1) {
+#pragma unroll
+            for (int j = 0; j < KT - 1; ++j) D[j] = D[j + 1];
+            D[KT - 1] = INFINITY;
+        }
+    }
+    if (lane == 0) {
+        *bound = t;
+        *counter = 0u;
+    }
+}
+
+template <int KT>
+static int nearest_one(const float *pts, int64_t n, float qx, float qy, int k, int64_t *idx, float *d,
+                       PairSlot *partials, unsigned *counter, const float *bound, int grid, cudaStream_t s) {
+    int rc = launch_guard("nearest_kernel");
+    if (rc != ACCR_OK) return rc;
+    nearest_kernel<KT, NK_THREADS><<<grid, NK_THREADS, 0, s>>>(pts, n, qx, qy, k, idx, d, partials, counter, bound);
+    return launched("nearest_kernel");
 }
 
 template <int KT>
@@ -369,15 +487,31 @@ static int nearest_launch(const float *pts, int64_t n, float qx, float qy, int k
         if (per_sm < 1) per_sm = 1;
     });
     const DeviceInfo &di = device_info();
-    int64_t want = (n / 2 + NT * 4 - 1) / (NT * 4);  // 4 vectors per thread
-    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
-    Scratch *scr = scratch_for((accr_stream_t)s, sizeof(PairSlot) * (size_t)grid * KT);
+    auto grid_for = [&](int64_t m) {
+        const int64_t want = (m / 2 + NT * 16 - 1) / (NT * 16);  // one round of 16 vectors per thread
+        return (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
+    };
+    const int grid = grid_for(n);
+    const bool use_bound = n >= NK_BOUND_MIN_N;
+    // scratch: [partials: grid * KT slots][the sample's warp minima][the bound]
+    const size_t part_bytes = sizeof(PairSlot) * (size_t)grid * KT;
+    const size_t lists_off = (part_bytes + 255) & ~(size_t)255;
+    const size_t bound_off = lists_off + sizeof(float) * NK_BOUND_WARPS;
+    Scratch *scr = scratch_for((accr_stream_t)s, use_bound ? bound_off + 16 : part_bytes);
     if (!scr) return ACCR_ENOMEM;
-    int rc = launch_guard("nearest_kernel");
-    if (rc != ACCR_OK) return rc;
-    nearest_kernel<KT, NT><<<grid, NT, 0, s>>>(pts, n, qx, qy, k, idx, d, (PairSlot *)scr->buf,
-                                                    scr->counters + 1);
-    return launched("nearest_kernel");
+    PairSlot *partials = (PairSlot *)scr->buf;
+    const float *bound = nullptr;
+    int rc;
+    if (use_bound) {
+        char *b = (char *)scr->buf;
+        float *bnd = (float *)(b + bound_off);
+        if ((rc = launch_guard("nearest_bound_kernel")) != ACCR_OK) return rc;
+        nearest_bound_kernel<KT><<<NK_BOUND_CTAS, NT, 0, s>>>((const float2 *)pts, n / NK_CHUNKS, qx, qy, k,
+                                                             (float *)(b + lists_off), scr->counters + 5, bnd);
+        if ((rc = launched("nearest_bound_kernel")) != ACCR_OK) return rc;
+        bound = bnd;
+    }
+    return nearest_one<KT>(pts, n, qx, qy, k, idx, d, partials, scr->counters + 1, bound, grid, s);
 }
 
 // ============================================================================

@@ -31,6 +31,34 @@ def test_nearest_k_exact(n, k):
         assert np.array_equal(d2.cpu().numpy(), wd), (n, k, off)
 
 
+@pytest.mark.parametrize("order", ["random", "far_first", "near_first", "all_equal"])
+@pytest.mark.parametrize("k", [1, 8, 16])
+def test_nearest_k_sampled_bound(order, k):
+    """Inputs large enough for the sampled distance bound: exact whatever the
+    order of the points (a sample of far points gives a loose bound, one of
+    near points a tight one, equal points put every point on the bound)."""
+    n = (1 << 22) + 5
+    g = inputs.rng(22, k)
+    pts = (g.random((n, 2), dtype=np.float32) * 100).astype(np.float32)
+    qx, qy = 50.0, 50.0
+    if order == "all_equal":
+        pts[:] = np.float32(12.5)
+    elif order != "random":
+        d = (pts[:, 0] - qx) ** 2 + (pts[:, 1] - qy) ** 2
+        pts = pts[np.argsort(-d if order == "far_first" else d, kind="stable")].copy()
+    pts[n - 1] = pts[n // 2]                  # an exact tie, broken by index
+    for off in [0, 1]:
+        big = np.zeros((n + off, 2), dtype=np.float32)
+        big[off:] = pts
+        pt = torch.from_numpy(big).cuda()[off:]
+        idx = torch.empty(k, dtype=torch.int64, device="cuda")
+        d2 = torch.empty(k, dtype=torch.float32, device="cuda")
+        api.accr_nearest_k(pt, qx, qy, k, idx, d2, flags=api.ACCR_SYNC)
+        wi, wd = oracle.nearest_k(pts, qx, qy, k)
+        assert np.array_equal(idx.cpu().numpy(), wi), (order, k, off)
+        assert np.array_equal(d2.cpu().numpy(), wd), (order, k, off)
+
+
 def test_nearest_k_rejects_bad_k():
     pts = torch.zeros((4, 2), device="cuda")
     i = torch.empty(32, dtype=torch.int64, device="cuda")
