@@ -724,10 +724,10 @@ def run_rows(args):
     return 0
 
 
-def measure_patterns(dev, reps=10):
-    """The survey's next rows: the paper's two-level host merge against the
-    single-pass merge (f1), the SRAD pattern fused and unfused (f2), the BFS
-    convergence flag in its three forms (f3), and k-nearest (f4)."""
+def measure_patterns(dev, reps=10, which=("f1", "f2", "f3", "f4")):
+    """The paper's two-level host merge against the single-pass merge (f1),
+    the SRAD pattern fused and unfused (f2), the BFS convergence flag in its
+    three forms (f3), and k-nearest (f4); `which` selects among them."""
     import torch
     from paper_1412_1127_gb300 import api, inputs
     stream = torch.cuda.current_stream(dev)
@@ -745,7 +745,7 @@ def measure_patterns(dev, reps=10):
 
     # f1: result of one region available on the host
     f1 = {}
-    for lg in (20, 24, 28):
+    for lg in ((20, 24, 28) if "f1" in which else ()):
         x = torch.from_numpy(inputs.full_range_i32(1 << lg, salt=lg)).to(dev)
         sd = torch.empty(1, dtype=torch.int64, device=dev)
         sh = torch.empty(1, dtype=torch.int64).pin_memory()
@@ -760,11 +760,12 @@ def measure_patterns(dev, reps=10):
         a, b = wall(single, reps), wall(two_level, reps)
         f1["2^%d" % lg] = {"single_pass_ms": round(a, 4), "two_level_host_ms": round(b, 4)}
         del x
-    out["f1_two_level_vs_single_pass"] = f1
+    if f1:
+        out["f1_two_level_vs_single_pass"] = f1
 
     # f2: SRAD pattern (statistics, then the standardised array)
     f2 = {}
-    for lg in (22, 28):
+    for lg in ((22, 28) if "f2" in which else ()):
         n = 1 << lg
         x = torch.from_numpy(inputs.normal(n, np.float32, salt=lg)).to(dev)
         y = torch.empty_like(x)
@@ -775,7 +776,17 @@ def measure_patterns(dev, reps=10):
             r[form] = {"ms": round(ms, 4), "gbs_3_passes": round(12.0 * n / (ms * 1e-3) / 1e9, 1)}
         f2["n=2^%d" % lg] = r
         del x, y
-    out["f2_srad_pattern"] = f2
+    if f2:
+        out["f2_srad_pattern"] = f2
+    if "f3" in which:
+        out["f3_bfs_convergence"] = measure_bfs(dev, api, inputs, stream, wall)
+    if "f4" in which:
+        out["f4_nearest_k5"] = measure_nearest(dev, api, inputs, stream, reps)
+    return out
+
+
+def measure_bfs(dev, api, inputs, stream, wall):
+    import torch
 
     # f3: BFS convergence loop on a 1024 x 1024 grid, 62 % open
     g = inputs.rng(23, 1)
@@ -792,9 +803,11 @@ def measure_patterns(dev, reps=10):
             lv[0] = api.accr_grid_bfs(gt, src, dist, mode=mode, stream=stream)
         ms = wall(run, 3)
         f3[mode] = {"ms": round(ms, 3), "levels": lv[0], "us_per_level": round(ms * 1e3 / max(lv[0], 1), 2)}
-    out["f3_bfs_convergence"] = f3
+    return f3
 
-    # f4: k = 5 nearest of 2^26 points
+
+def measure_nearest(dev, api, inputs, stream, reps):
+    import torch
     n = 1 << 26
     pts = torch.from_numpy((inputs.rng(21, 5).random((n, 2), dtype=np.float32) * 100)).to(dev)
     idx = torch.empty(5, dtype=torch.int64, device=dev)
@@ -809,14 +822,14 @@ def measure_patterns(dev, reps=10):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    out["f4_nearest_k5"] = {"n": n, "ms": round(ms, 4), "gbs": round(8.0 * n / (ms * 1e-3) / 1e9, 1)}
-    return out
+    return {"n": n, "ms": round(ms, 4), "gbs": round(8.0 * n / (ms * 1e-3) / 1e9, 1)}
 
 
 def run_patterns(args):
     import torch
     torch.cuda.set_device(0)
-    print(json.dumps(measure_patterns(torch.device("cuda", 0))), flush=True)
+    which = tuple(w.strip() for w in args.patterns.split(",") if w.strip())
+    print(json.dumps(measure_patterns(torch.device("cuda", 0), which=which)), flush=True)
     return 0
 
 
@@ -845,6 +858,7 @@ def main():
     ap.add_argument("--workload", default="scalar", choices=["scalar", "batched", "served", "matmul", "rows", "patterns"])
     ap.add_argument("--len", type=int, default=4096, help="matmul: LEN")
     ap.add_argument("--rows-m", type=int, default=65536, help="rows: number of rows (4096 columns)")
+    ap.add_argument("--patterns", default="f1,f2,f3,f4", help="patterns: which of f1,f2,f3,f4 to run")
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--rate", type=float, default=50000.0)
     ap.add_argument("--no-extra", action="store_true",
