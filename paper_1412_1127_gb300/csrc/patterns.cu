@@ -743,6 +743,7 @@ __global__ void map_kernel(const float *x, float *y, int64_t n, const StdShared 
 // ============================================================================
 
 constexpr int BF_THREADS = 256;
+constexpr int BFP_THREADS = 1024;  // the persistent form: one CTA per SM
 
 __global__ void bfs_init_kernel(int32_t *dist, int64_t total, int64_t src, const uint8_t *open) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x)
@@ -751,18 +752,42 @@ __global__ void bfs_init_kernel(int32_t *dist, int64_t total, int64_t src, const
 
 // One level, pull form: an unvisited open cell with a neighbour at level L
 // joins level L + 1.  Returns whether this thread changed any cell.
+// One level of the pull formulation over the thread's cells, CU cells at a
+// time with every load of a group issued before any is tested: the level is
+// bound by L2 latency, not bandwidth, at the sizes of the BFS workloads.
 __device__ __forceinline__ bool bfs_level(const uint8_t *__restrict__ open, int32_t *dist, int64_t rows,
                                           int64_t cols, int32_t L) {
-    const int64_t total = rows * cols;
+    constexpr int CU = 4;
+    const int64_t total = rows * cols;  // < 2^31 (checked on the host): 32-bit cell arithmetic
+    const uint32_t ucols = (uint32_t)cols, urows = (uint32_t)rows;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     bool changed = false;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
-        if (__ldcg(dist + c) != -1 || !__ldg(open + c)) continue;
-        const int64_t r = c / cols, q = c - r * cols;
-        const bool hit = (r > 0 && __ldcg(dist + c - cols) == L) || (r + 1 < rows && __ldcg(dist + c + cols) == L) ||
-                         (q > 0 && __ldcg(dist + c - 1) == L) || (q + 1 < cols && __ldcg(dist + c + 1) == L);
-        if (hit) {
-            dist[c] = L + 1;
-            changed = true;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c0 < total; c0 += CU * nth) {
+        int32_t d[CU];
+        bool need[CU];
+#pragma unroll
+        for (int j = 0; j < CU; ++j) {
+            const int64_t c = c0 + j * nth;
+            d[j] = c < total ? __ldcg(dist + c) : 0;
+            need[j] = c < total && __ldg(open + c) != 0;
+        }
+        int32_t nb[CU][4];
+#pragma unroll
+        for (int j = 0; j < CU; ++j) {  // an unvisited open cell reads its four neighbours
+            const uint32_t c = (uint32_t)(c0 + j * nth);
+            const bool go = need[j] && d[j] == -1;
+            const uint32_t r = c / ucols, q = c - r * ucols;
+            nb[j][0] = go && r > 0 ? __ldcg(dist + c - ucols) : -2;
+            nb[j][1] = go && r + 1 < urows ? __ldcg(dist + c + ucols) : -2;
+            nb[j][2] = go && q > 0 ? __ldcg(dist + c - 1) : -2;
+            nb[j][3] = go && q + 1 < ucols ? __ldcg(dist + c + 1) : -2;
+        }
+#pragma unroll
+        for (int j = 0; j < CU; ++j) {
+            if (nb[j][0] == L || nb[j][1] == L || nb[j][2] == L || nb[j][3] == L) {
+                dist[c0 + j * nth] = L + 1;
+                changed = true;
+            }
         }
     }
     return changed;
@@ -799,28 +824,28 @@ __global__ void __launch_bounds__(BF_THREADS) bfs_level_kernel(const uint8_t *__
 
 // All levels in one cooperative launch: per level, the || of the changed
 // flags goes to a per-level slot, a bounded grid barrier separates levels.
-__global__ void __launch_bounds__(BF_THREADS) bfs_persistent_kernel(const uint8_t *__restrict__ open, int32_t *dist,
-                                                                    int64_t rows, int64_t cols, unsigned *flags,
-                                                                    int64_t max_levels, unsigned *bar,
-                                                                    int64_t *levels_out, int *err) {
+// One CTA of BFP_THREADS per SM (fewer arrivals per grid barrier), one
+// barrier per level.  The flag of level L lives in slot L % 3: it is written
+// before barrier L and read after it; block 0 clears slot (L + 1) % 3 during
+// level L, when every CTA has passed barrier L - 1 and so has finished
+// reading that slot (last used by level L - 2), and before anyone can write
+// it (level L + 1, after barrier L).
+__global__ void __launch_bounds__(BFP_THREADS, 1) bfs_persistent_kernel(const uint8_t *__restrict__ open, int32_t *dist,
+                                                                       int64_t rows, int64_t cols, unsigned *flags,
+                                                                       int64_t max_levels, unsigned *bar,
+                                                                       int64_t *levels_out, int *err) {
     unsigned gen = *(volatile unsigned *)&bar[1];
     int64_t L = 0;
     for (; L < max_levels; ++L) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(L + 1) % 3] = 0u;
         const bool changed = bfs_level(open, dist, rows, cols, (int32_t)L);
         const int any = __syncthreads_or(changed ? 1 : 0);
-        if (threadIdx.x == 0 && any) atomicOr(&flags[L & 1], 1u);
+        if (threadIdx.x == 0 && any) atomicOr(&flags[L % 3], 1u);
         if (!grid_barrier(bar, gen)) {
             if (threadIdx.x == 0) atomicExch(err, 7);
             return;
         }
-        const unsigned f = *(volatile unsigned *)&flags[L & 1];
-        // clear the other slot for the next level; every CTA has read it already
-        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(L + 1) & 1] = 0u;
-        if (!grid_barrier(bar, gen)) {
-            if (threadIdx.x == 0) atomicExch(err, 7);
-            return;
-        }
-        if (!f) break;
+        if (!*(volatile unsigned *)&flags[L % 3]) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *levels_out = L + 1;  // the level that found nothing new
 }
@@ -976,7 +1001,7 @@ extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t
     static int per_sm = 0;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_persistent_kernel, BF_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_kernel, BF_THREADS, 0);
         if (per_sm < 1) per_sm = 1;
     });
     const int64_t want = (total + BF_THREADS - 1) / BF_THREADS;
@@ -985,7 +1010,7 @@ extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t
     if (!scr) return ACCR_ENOMEM;
     unsigned *more = scr->counters + 8;
     unsigned *counter = scr->counters + 9;
-    unsigned *flags2 = scr->counters + 10;   // two level slots
+    unsigned *flags3 = scr->counters + 16;   // three level slots (persistent form)
     unsigned *bar = scr->counters + 12;      // arrivals, generation
     int *err = (int *)(scr->counters + 14);
     int64_t *lv = (int64_t *)((char *)scr->buf);
@@ -994,14 +1019,15 @@ extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t
     if (!hmore) return ACCR_ENOMEM;
     if (mode == ACCR_BFS_PERSISTENT) {
         rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_grid_bfs: clear status");
-        if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(flags2, 0, 2 * sizeof(unsigned), s), "accr_grid_bfs: flags");
+        if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(flags3, 0, 3 * sizeof(unsigned), s), "accr_grid_bfs: flags");
         if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(bar, 0, sizeof(unsigned), s), "accr_grid_bfs: barrier");
         if (rc != ACCR_OK) return rc;
         int64_t maxl = total + 1;
-        void *args[] = {(void *)&open, (void *)&dist, (void *)&rows, (void *)&cols, (void *)&flags2, (void *)&maxl,
+        void *args[] = {(void *)&open, (void *)&dist, (void *)&rows, (void *)&cols, (void *)&flags3, (void *)&maxl,
                         (void *)&bar, (void *)&lv, (void *)&err};
         if ((rc = launch_guard("bfs_persistent_kernel")) != ACCR_OK) return rc;
-        rc = cuda_check(cudaLaunchCooperativeKernel((const void *)bfs_persistent_kernel, grid, BF_THREADS, args, 0, s),
+        const int pgrid = (int)std::min<int64_t>((total + BFP_THREADS - 1) / BFP_THREADS, (int64_t)di.sms);
+        rc = cuda_check(cudaLaunchCooperativeKernel((const void *)bfs_persistent_kernel, pgrid, BFP_THREADS, args, 0, s),
                         "accr_grid_bfs: cooperative launch");
         if (rc != ACCR_OK) return rc;
         if ((rc = launched("bfs_persistent_kernel")) != ACCR_OK) return rc;

@@ -126,3 +126,22 @@ def test_grid_bfs_closed_source():
     for mode in ["reduce", "guarded", "persistent"]:
         assert api.accr_grid_bfs(gt, 9, dist, mode=mode) == 0
         assert bool((dist == -1).all())
+
+
+def test_grid_bfs_serpentine_many_levels():
+    """A one-cell-wide winding corridor: thousands of levels, each adding one
+    cell, so every level's flag slot is reused many times; repeated calls
+    re-arm the grid barrier."""
+    rows, cols = 41, 96
+    grid = np.zeros((rows, cols), dtype=np.uint8)
+    grid[0::2, :] = 1                      # open corridors on even rows
+    for r in range(1, rows, 2):            # one opening per wall row, alternating ends
+        grid[r, cols - 1 if (r // 2) % 2 == 0 else 0] = 1
+    src = 0
+    want, wl = oracle.grid_bfs(grid, src)
+    assert wl > 2000
+    gt = torch.from_numpy(grid).cuda()
+    for mode in ["persistent", "persistent", "guarded", "persistent"]:
+        dist = torch.empty((rows, cols), dtype=torch.int32, device="cuda")
+        assert api.accr_grid_bfs(gt, src, dist, mode=mode) == wl
+        assert np.array_equal(dist.cpu().numpy(), want)
