@@ -32,6 +32,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -217,6 +218,41 @@ def cpu_time_sample(host, regions, n):
     return time.perf_counter() - t0
 
 
+def cpu_model():
+    """Host CPU as the kernel reports it, and the number of cores."""
+    name = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    name += " " + line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": name, "cores": os.cpu_count()}
+
+
+def cpu_all_cores(host, regions, n):
+    """The same oracle sample with one region per host thread, all cores busy
+    (the oracle is unchanged: each call is one serial region; ctypes releases
+    the interpreter lock for the call)."""
+    import concurrent.futures as cf
+    import oracle
+    cores = min(os.cpu_count() or 1, len(regions))
+    oracle.reduce(host["i32"][:1024], "add", "i64")  # load the library before timing
+
+    def one(r):
+        _, kind, op, acc, _ = r
+        oracle.reduce(host[kind][:n], op, acc)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, regions))
+    dt = time.perf_counter() - t0
+    sb = sum(n * ELEM[k] for _, k, _, _, _ in regions)
+    return {"value": round(sb / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "seconds": round(dt, 2)}
+
+
 def run_reference(args):
     """--impl reference: the serial oracle on the host cores, bounded sample."""
     rank, world, _ = dist_env()
@@ -363,7 +399,8 @@ def run_scalar(args):
         sb = sum(sample * ELEM[k] for _, k, _, _, _ in SCALAR_REGIONS)
         cpu = {"value": round(sb / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "first 2^26 elements of each of the 16 regions (1/4 of a step), serial C",
-               "seconds": round(dt, 2)}
+               "seconds": round(dt, 2), "cpu": cpu_model(),
+               "all_cores": cpu_all_cores(host, SCALAR_REGIONS, sample)}
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
@@ -382,6 +419,8 @@ def run_scalar(args):
         extra["rows"] = measure_rows(dev)
         torch.cuda.empty_cache()
         extra["patterns"] = measure_patterns(dev)
+        torch.cuda.empty_cache()
+        extra["one_region_2e20"] = measure_small_region(dev)
 
     if rank == 0:
         line = {
@@ -669,7 +708,7 @@ def measure_matmul(dev, length=4096, reps=5):
         if mode == "bf16x3":
             r["tensor_tflops"] = round(3 * flops / (ms * 1e-3) / 1e12, 2)
             r["frac_of_bf16_peak"] = round(3 * flops / (ms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]), 4)
-            r["note"] = "time includes the two split kernels; tensor work is 3 products"
+            r["note"] = "time includes the split kernel; tensor work is 3 products"
             # repeated nest with unchanged operands: the split is reused, so this is the GEMM alone
             fl = api.ACCR_MM_REUSE_SPLIT
             api.accr_matmul_nest(at, bt, ct, mode=mode, flags=fl, stream=stream)
@@ -684,6 +723,79 @@ def measure_matmul(dev, length=4096, reps=5):
             r["reuse_split_tensor_tflops"] = round(3 * flops / (gms * 1e-3) / 1e12, 2)
             r["reuse_split_frac_of_bf16_peak"] = round(3 * flops / (gms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]), 4)
         out[mode] = r
+    fp32 = measure_fp32_peak(dev)
+    out["fp32_peak"] = fp32
+    for mode in ("simt", "serial"):
+        out[mode]["frac_of_fp32_peak"] = round(out[mode]["tflops"] / fp32["tflops"], 4)
+    return out
+
+
+def measure_fp32_peak(dev, rounds=1 << 15, reps=5):
+    """Measured FP32 FMA peak (the SIMT nest's roofline): 16 independent FMA
+    chains per thread, 4 CTAs of 256 threads per SM."""
+    import torch
+    from paper_1412_1127_gb300 import api
+    ctas = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(256 * ctas, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        api.accr_probe_fma(ctas, rounds, sink, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        api.accr_probe_fma(ctas, rounds, sink, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flop = 2.0 * 16 * 256 * ctas * rounds
+    return {"tflops": round(flop / (ms * 1e-3) / 1e12, 2), "ms": round(ms, 4),
+            "probe": "%d CTAs x 256 threads x %d rounds x 16 FMA" % (ctas, rounds)}
+
+
+def measure_small_region(dev, n=1 << 20, reps=100):
+    """One region of 2^20 int32 U[-1000, 1000] with reduction(+:s) into a
+    64-bit variable and reduction(max:m): device time per region, inputs warm
+    in L2 and with L2 flushed before each region (a 2 x L2 write between
+    regions, outside the timed interval).  A 4 MiB region takes a few
+    microseconds, less than one host call, so the calls are queued behind a
+    long FMA probe launch and each region is bracketed by its own events; the
+    host time per call is reported beside it."""
+    import torch
+    from paper_1412_1127_gb300 import api, inputs
+    x = torch.from_numpy(inputs.scalar_i32_small(n)).to(dev)
+    s_ = torch.empty(1, dtype=torch.int64, device=dev)
+    m_ = torch.empty(1, dtype=torch.int32, device=dev)
+    cls = [api.clause("add", s_), api.clause("max", m_)]
+    stream = torch.cuda.current_stream(dev)
+    l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (128 << 20))
+    flush = torch.empty(2 * l2 // 4, dtype=torch.int32, device=dev)
+    ctas = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(256 * ctas, dtype=torch.float32, device=dev)
+    out = {"workload": "one region, 2^20 int32, + (int64 variable) and max in one pass"}
+    for mode in ("warm", "l2_flushed"):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for _ in range(5):
+            api.accr_reduce(x, cls, stream=stream)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        api.accr_probe_fma(ctas, 1 << 18, sink, stream=stream)  # the GPU is busy while the host queues
+        b1.record(stream)
+        t0 = time.perf_counter()
+        for e0, e1 in evs:
+            if mode == "l2_flushed":
+                flush.fill_(1)
+            e0.record(stream)
+            api.accr_reduce(x, cls, stream=stream)
+            e1.record(stream)
+        host_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        us = sorted(e0.elapsed_time(e1) * 1e3 for e0, e1 in evs)
+        med = us[len(us) // 2]
+        out[mode] = {"us_per_region_median": round(med, 2), "gbs": round(4.0 * n / (med * 1e-6) / 1e9, 1),
+                     "host_us_per_call": round(host_s * 1e6 / reps, 2),
+                     "queued_ahead": bool(host_s * 1e3 < b0.elapsed_time(b1))}
     return out
 
 
@@ -859,7 +971,7 @@ def main():
     ap.add_argument("--len", type=int, default=4096, help="matmul: LEN")
     ap.add_argument("--rows-m", type=int, default=65536, help="rows: number of rows (4096 columns)")
     ap.add_argument("--patterns", default="f1,f2,f3,f4", help="patterns: which of f1,f2,f3,f4 to run")
-    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-seconds", type=float, default=10.0)
     ap.add_argument("--rate", type=float, default=50000.0)
     ap.add_argument("--no-extra", action="store_true",
                     help="scalar workload only (skip the batched and served sub-measurements)")

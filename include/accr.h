@@ -431,6 +431,18 @@ ACCR_API int accr_fault_inject(int32_t kind, int64_t count);
  * context stays usable. */
 ACCR_API int accr_selftest_wait_timeout(uint32_t tries, accr_stream_t stream);
 
+/* ---- measurement support -------------------------------------------------------- */
+
+/* FP32 peak probe, the denominator of the SIMT matrix nest's roofline (no
+ * counterpart in the paper): `ctas` CTAs of 256 threads each run `rounds`
+ * rounds of 16 independent fused multiply-adds per thread, i.e.
+ * 2 * 16 * 256 * ctas * rounds flop, then write one float per thread to
+ * `sink` (device memory, caller-owned, at least 256 * ctas floats; every value
+ * ends near 1.0) so that no work can be dropped.  Asynchronous on `stream`;
+ * time it with events on that stream.  ACCR_EINVAL for ctas < 1, rounds < 1
+ * or a NULL sink. */
+ACCR_API int accr_probe_fma(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream);
+
 /* Message of the last error raised on the calling thread ("" if none). */
 ACCR_API const char *accr_last_error(void);
 

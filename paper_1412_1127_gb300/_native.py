@@ -76,6 +76,7 @@ SIGNATURES = {
     "accr_reduce_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _CP, _i32, _u32, _vp]),
     "accr_fault_inject": (ctypes.c_int, [_i32, _i64]),
     "accr_selftest_wait_timeout": (ctypes.c_int, [_u32, _vp]),
+    "accr_probe_fma": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
     "accr_last_error": (ctypes.c_char_p, []),
     "accr_launch_count": (_u64, []),
     "accr_version": (_i32, []),

@@ -315,6 +315,13 @@ def accr_fault_inject(kind, count):
     return check(lib().accr_fault_inject(int(kind), int(count)))
 
 
+def accr_probe_fma(ctas, rounds, sink, stream=None):
+    """FP32 peak probe (2 * 16 * 256 * ctas * rounds flop); sink: CUDA float
+    tensor of at least 256 * ctas elements."""
+    assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= 256 * ctas
+    return check(lib().accr_probe_fma(int(ctas), int(rounds), sink.data_ptr(), _stream(stream)))
+
+
 def accr_selftest_wait_timeout(tries=1000, stream=None):
     """Runs the bounded-wait self-test; returns its status code (ACCR_ETIMEDOUT expected)."""
     return int(lib().accr_selftest_wait_timeout(int(tries), _stream(stream)))

@@ -154,6 +154,25 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
     }
 }
 
+// FP32 peak probe: 16 independent FMA chains per thread (latency hidden by
+// the chains and by 8 warps per SM sub-partition at 4 CTAs per SM); b and c
+// keep every chain bounded (x -> 0.999 x + 0.001 tends to 1).
+constexpr int PROBE_THREADS = 256;
+
+__global__ void __launch_bounds__(PROBE_THREADS) fma_probe_kernel(int64_t rounds, float *sink, float b, float c) {
+    float a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = (float)(threadIdx.x + i) * 1e-3f;
+    for (int64_t r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a[i] = __fmaf_rn(a[i], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += a[i];
+    sink[(int64_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = s * (1.f / 16.f);
+}
+
 int matmul_simt(const float *a, const float *b, float *c, int64_t len, bool serial, cudaStream_t s) {
     if (len == 0) return ACCR_OK;
     const int64_t tiles = (len + MT - 1) / MT;
@@ -174,3 +193,12 @@ int matmul_simt(const float *a, const float *b, float *c, int64_t len, bool seri
 }
 
 }  // namespace accr
+
+extern "C" ACCR_API int accr_probe_fma(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream) {
+    accr::clear_error();
+    if (ctas < 1 || rounds < 1 || !sink) return accr::set_error(ACCR_EINVAL, "accr_probe_fma: bad arguments");
+    int rc = accr::launch_guard("fma_probe_kernel");
+    if (rc != ACCR_OK) return rc;
+    accr::fma_probe_kernel<<<ctas, accr::PROBE_THREADS, 0, (cudaStream_t)stream>>>(rounds, sink, 0.999f, 0.001f);
+    return accr::launched("fma_probe_kernel");
+}

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fold.cuh"
@@ -52,7 +53,10 @@ __device__ __forceinline__ Partial ld_partial(const Partial *p) {
     return q;
 }
 
-template <typename T, int NC>
+// W0 / W1 >= 0 fix the working codes of clauses 0 / 1 at compile time (the
+// operator switches fold away and the kernel's code shrinks to what the two
+// operators need); -1 reads them from the arguments.
+template <typename T, int NC, int W0 = -1, int W1 = -1>
 __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ ReduceArgs p) {
     constexpr bool E64 = sizeof(T) == 8;
     constexpr int EPV = 16 / (int)sizeof(T);
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ R
     Acc A[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        w[c] = p.cl[c].wcode;
+        w[c] = (c == 0 && W0 >= 0) ? W0 : (c == 1 && W1 >= 0) ? W1 : p.cl[c].wcode;
         ident[c] = p.cl[c].ident;
         A[c].a = ident[c];
         A[c].c = 0.f;
@@ -176,16 +180,55 @@ static int occupancy_grid() {
     return slot;
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int W0 = -1, int W1 = -1>
 static int launch_t(ReduceArgs &a, int grid, cudaStream_t s) {
     int rc = launch_guard("reduce_kernel");
     if (rc != ACCR_OK) return rc;
-    reduce_kernel<T, NC><<<grid, RB, 0, s>>>(a);
+    reduce_kernel<T, NC, W0, W1><<<grid, RB, 0, s>>>(a);
     return launched("reduce_kernel");
+}
+
+// A sum together with a max or a min -- the two-clause region of the paper's
+// examples, reduction(+:s) reduction(max:m) -- runs a kernel with both codes
+// fixed: the generic two-clause kernel carries every operator's code twice
+// over, and on small regions its instruction fetch costs more than the data.
+// The clause order is canonical (sum first) here: each clause descriptor
+// carries its own output, and the kernel merges its own partials.  The grid
+// stays the generic kernel's, so results do not depend on which one runs.
+template <typename T, int W0, int W1>
+static bool pair_t(ReduceArgs &a, int grid, cudaStream_t s, int &rc) {
+    if (a.cl[0].wcode != W0 || a.cl[1].wcode != W1) return false;
+    rc = launch_t<T, 2, W0, W1>(a, grid, s);
+    return true;
+}
+
+template <typename T>
+static bool launch_pair(ReduceArgs &a, int grid, cudaStream_t s, int &rc) {
+    auto is_sum = [](int w) { return w == W_ADD32 || w == W_ADD64 || w == W_ADDF || w == W_ADDF_COMP || w == W_ADDF_WIDE; };
+    if (!is_sum(a.cl[0].wcode) && is_sum(a.cl[1].wcode)) {
+        const ClauseDev t = a.cl[0];
+        a.cl[0] = a.cl[1];
+        a.cl[1] = t;
+    }
+    if constexpr (std::is_same<T, int32_t>::value) {
+        return pair_t<T, W_ADD32, W_MAXI>(a, grid, s, rc) || pair_t<T, W_ADD32, W_MINI>(a, grid, s, rc) ||
+               pair_t<T, W_ADD64, W_MAXI>(a, grid, s, rc) || pair_t<T, W_ADD64, W_MINI>(a, grid, s, rc);
+    } else if constexpr (std::is_same<T, int64_t>::value) {
+        return pair_t<T, W_ADD64, W_MAXI>(a, grid, s, rc) || pair_t<T, W_ADD64, W_MINI>(a, grid, s, rc);
+    } else if constexpr (std::is_same<T, float>::value) {
+        return pair_t<T, W_ADDF, W_MAXF>(a, grid, s, rc) || pair_t<T, W_ADDF, W_MINF>(a, grid, s, rc) ||
+               pair_t<T, W_ADDF_COMP, W_MAXF>(a, grid, s, rc) || pair_t<T, W_ADDF_COMP, W_MINF>(a, grid, s, rc) ||
+               pair_t<T, W_ADDF_WIDE, W_MAXF>(a, grid, s, rc) || pair_t<T, W_ADDF_WIDE, W_MINF>(a, grid, s, rc);
+    } else {
+        return pair_t<T, W_ADDF, W_MAXF>(a, grid, s, rc) || pair_t<T, W_ADDF, W_MINF>(a, grid, s, rc);
+    }
 }
 
 template <typename T>
 static int launch_nc(ReduceArgs &a, int grid, cudaStream_t s) {
+    int rc = ACCR_OK;
+    // the two-level form merges the partials on the host in the caller's clause order
+    if (a.nc == 2 && !a.two_level && launch_pair<T>(a, grid, s, rc)) return rc;
     switch (a.nc) {
     case 1: return launch_t<T, 1>(a, grid, s);
     case 2: return launch_t<T, 2>(a, grid, s);

@@ -106,3 +106,14 @@ def test_reuse_split_flag():
     api.accr_matmul_nest(at, bt2, c2, mode="bf16x3", flags=api.ACCR_SYNC | api.ACCR_MM_REUSE_SPLIT)
     t, s = oracle.matmul_truth(a, b2)
     assert np.max(np.abs(c2.cpu().numpy() - t) / s) <= 1e-4
+
+
+def test_fma_probe():
+    """The FP32 peak probe runs its chains to the fixed point 1.0 and rejects
+    bad arguments on the host."""
+    sink = torch.zeros(256 * 8, dtype=torch.float32, device="cuda")
+    api.accr_probe_fma(8, 20000, sink)
+    s = sink.cpu().numpy()
+    assert np.all(np.abs(s - 1.0) < 1e-3), (s.min(), s.max())
+    with pytest.raises(api._native.AccrError):
+        api.accr_probe_fma(0, 10, sink)

@@ -285,3 +285,40 @@ def test_full_size_all_operators():
     out = torch.empty(1, dtype=torch.float64, device="cuda")
     api.accr_reduce(td, [api.clause("add", out)])
     assert_sum_close(out.item(), xd, TOL_F64)
+
+
+REDUCE_PAIRS = [  # (element type, sum variable, flags) of the fixed-code two-clause kernels
+    ("i32", "i32", 0), ("i32", "i64", 0), ("i64", "i64", 0), ("f32", "f32", 0),
+    ("f32", "f32", api.ACCR_COMPENSATED), ("f32", "f64", 0), ("f64", "f64", 0)]
+
+
+@pytest.mark.parametrize("t,acc,flags", REDUCE_PAIRS)
+@pytest.mark.parametrize("ext", ["max", "min"])
+@pytest.mark.parametrize("sum_first", [True, False])
+@pytest.mark.parametrize("n", [1, 33, 65536 + 7, (1 << 20) + 3])
+@pytest.mark.parametrize("two_level", [False, True])
+def test_sum_and_extreme_pairs(t, acc, flags, ext, sum_first, n, two_level):
+    """reduction(+:s) reduction(max|min:m) in one pass, in either clause order,
+    through the fixed-code kernels (and the generic one in the two-level
+    form): each variable gets its own fold (integers and extremes bit-exact,
+    float sums within the sum tolerance)."""
+    if t in ("i32", "i64"):
+        x = int_input("add", n, t, salt=n % 89)
+    else:
+        x = inputs.normal(n, ND[t], salt=n % 89)
+    xt = to_dev(x)
+    where = "cpu" if two_level else "cuda"  # the two-level form merges into host variables
+    s = torch.full((1,), 7, dtype=TD[acc], device=where)
+    m = torch.full((1,), 7, dtype=TD[t], device=where)
+    cls = [api.clause("add", s, 3 if t in ("i32", "i64") else None), api.clause(ext, m)]
+    fl = flags | (api.ACCR_TWO_LEVEL_HOST if two_level else 0)
+    api.accr_reduce(xt, cls if sum_first else cls[::-1], flags=fl)
+    got_s, got_m = s.cpu().numpy()[0], m.cpu().numpy()[0]
+    want_m = oracle.reduce(x, ext, t)
+    if t in ("i32", "i64"):
+        assert got_m == want_m
+        assert got_s == oracle.reduce(x, "add", acc, init=3)
+        return
+    assert same_bits(np.array([got_m]), np.array([want_m]))
+    tol = TOL_F32_COMP if flags else (TOL_F64 if acc == "f64" else TOL_F32)
+    assert_sum_close(float(got_s), x, tol)
