@@ -20,8 +20,8 @@ from . import api
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(HERE, "tuning.json")
 
-SMALL_CANDIDATES = [16384, 65536, 262144]
-TILE_CANDIDATES = [131072, 262144, 524288, 1048576, 2097152]
+SMALL_CANDIDATES = [4096, 16384, 32768, 65536, 131072]
+TILE_CANDIDATES = [262144, 524288, 1048576, 2097152, 4194304]
 
 
 def time_batch(regions, small, tile, reps=5, stream=None):
