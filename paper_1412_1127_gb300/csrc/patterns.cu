@@ -3,9 +3,11 @@
 //
 //  * Nearest Neighbor: distances to a query point and the k smallest -- a
 //    reduction whose operator keeps a sorted list of k (distance, index)
-//    pairs.  Each thread keeps its list in registers, a warp merges its 32
-//    lists by popping the smallest head k times (butterfly argmin), the CTA
-//    merges its warps' lists, and the last CTA to finish merges the CTA lists.
+//    pairs.  Each warp keeps one list in shared memory and tests a whole round
+//    of its points against the list's k-th distance at once; a distance bound
+//    taken from a sample of the points first (a separate small launch) keeps
+//    the lists' slow path rare.  The CTA ranks its warps' entries, and the
+//    last CTA to finish merges the CTA lists.
 //
 //  * SRAD: a reduction region whose result feeds a data-parallel region.  The
 //    paper's OpenACC code merges the block partials on the CPU and launches
@@ -171,9 +173,8 @@ __device__ __forceinline__ float sqdist(float x, float y, float qx, float qy) {
 // One list per warp in shared memory; every lane keeps the warp's current
 // k-th entry (the threshold) in registers.  A lane's candidate that beats the
 // threshold is found by a ballot; such candidates (rare once the list has
-// filled) go through the out-of-line slow path one at a time, lane 0 inserting
-// into the shared list.  The expected number of insertions per warp grows
-// only with the log of the points it scans.
+// filled, or from the start under the sampled bound) go through the
+// out-of-line slow path one at a time, lane 0 inserting into the shared list.
 struct Thr {
     float d;
     int64_t i;
