@@ -145,3 +145,17 @@ def test_grid_bfs_serpentine_many_levels():
         dist = torch.empty((rows, cols), dtype=torch.int32, device="cuda")
         assert api.accr_grid_bfs(gt, src, dist, mode=mode) == wl
         assert np.array_equal(dist.cpu().numpy(), want)
+
+
+@pytest.mark.slow
+def test_nearest_k_full_size():
+    """k = 5 nearest of the 2^26 points bench.py times (same generator)."""
+    n = 1 << 26
+    pts = (inputs.rng(21, 5).random((n, 2), dtype=np.float32) * 100).astype(np.float32)
+    pt = torch.from_numpy(pts).cuda()
+    idx = torch.empty(5, dtype=torch.int64, device="cuda")
+    d2 = torch.empty(5, dtype=torch.float32, device="cuda")
+    api.accr_nearest_k(pt, 41.5, 58.25, 5, idx, d2, flags=api.ACCR_SYNC)
+    wi, wd = oracle.nearest_k(pts, 41.5, 58.25, 5)
+    assert np.array_equal(idx.cpu().numpy(), wi)
+    assert np.array_equal(d2.cpu().numpy(), wd)

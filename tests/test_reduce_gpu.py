@@ -322,3 +322,23 @@ def test_sum_and_extreme_pairs(t, acc, flags, ext, sum_first, n, two_level):
     assert same_bits(np.array([got_m]), np.array([want_m]))
     tol = TOL_F32_COMP if flags else (TOL_F64 if acc == "f64" else TOL_F32)
     assert_sum_close(float(got_s), x, tol)
+
+
+@pytest.mark.slow
+def test_region_beyond_2_31_elements():
+    """One region of 2^31 + 77 int32 (8.6 GB): 64-bit index arithmetic all the
+    way to the last element (the extremes are planted past 2^31)."""
+    n = (1 << 31) + 77
+    x = inputs.full_range_i32(n, salt=31)
+    x[n - 1] = np.int32(2 ** 31 - 1)
+    x[(1 << 31) + 5] = np.int32(-(2 ** 31))
+    xt = torch.from_numpy(x).cuda()
+    s = torch.empty(1, dtype=torch.int64, device="cuda")
+    m = torch.empty(1, dtype=torch.int32, device="cuda")
+    lo = torch.empty(1, dtype=torch.int32, device="cuda")
+    xo = torch.empty(1, dtype=torch.int32, device="cuda")
+    api.accr_reduce(xt, [api.clause("add", s), api.clause("max", m)])   # fixed-code pair
+    api.accr_reduce(xt, [api.clause("min", lo), api.clause("bxor", xo)])  # generic pair
+    assert s.item() == oracle.reduce(x, "add", "i64")
+    assert m.item() == 2 ** 31 - 1 and lo.item() == -(2 ** 31)
+    assert xo.item() == oracle.reduce(x, "bxor", "i32")
