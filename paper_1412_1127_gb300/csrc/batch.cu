@@ -314,6 +314,7 @@ struct HostPlan {
     std::vector<int32_t> small;   // queue order
     int64_t ntiles = 0;           // partial slots
     int64_t tile_bytes = ACCR_TILE_BYTES;
+    int64_t tile_override = 0;    // > 0: this plan's tile size instead of the process-wide one
     // layout of the device copy
     size_t off_tiles = 0, off_small = 0, off_partials = 0, plan_bytes = 0, total_bytes = 0;
 };
@@ -331,7 +332,7 @@ static int log2_floor(uint64_t v) {
 // that neighbouring work runs the same code, largest first within a group so
 // that the small pieces fill in at the end.  (Counting sort on a size bucket.)
 static int finish_plan(HostPlan &P) {
-    const int64_t small_b = g_small_bytes.load(), tile_b = g_tile_bytes.load();
+    const int64_t small_b = g_small_bytes.load(), tile_b = P.tile_override > 0 ? P.tile_override : g_tile_bytes.load();
     P.tile_bytes = tile_b;
     P.tiles.clear();
     P.small.clear();
@@ -607,8 +608,9 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
     return ACCR_OK;
 }
 
-int batch_launch_regions(const accr_region *regions, int64_t nregions, accr_stream_t stream) {
+int batch_launch_regions(const accr_region *regions, int64_t nregions, accr_stream_t stream, int64_t tile_bytes) {
     HostPlan P;
+    P.tile_override = tile_bytes;
     int rc = plan_from_regions(regions, nregions, P);
     if (rc != ACCR_OK) return rc;
     return run_once(P, 0, stream);

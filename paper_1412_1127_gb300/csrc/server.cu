@@ -149,7 +149,7 @@ int accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
         for (int c = 0; c < regs[i].nclauses; ++c) regs[i].clauses[c].out = &s.dev_res[i * ACCR_MAX_CLAUSES + c];
     }
     s.launch_ns = now_ns();
-    int rc = batch_launch_regions(regs.data(), (int64_t)regs.size(), (accr_stream_t)s.stream);
+    int rc = batch_launch_regions(regs.data(), (int64_t)regs.size(), (accr_stream_t)s.stream, ACCR_SERVED_TILE_BYTES);
     if (rc == ACCR_OK)
         rc = cuda_check(cudaMemcpyAsync(s.host_res, s.dev_res, sizeof(uint64_t) * ACCR_MAX_CLAUSES * regs.size(),
                                         cudaMemcpyDeviceToHost, s.stream),
