@@ -270,9 +270,9 @@ ACCR_API int accr_batch_tiling(int64_t small_bytes, int64_t tile_bytes,
 #define ACCR_TILE_BYTES 2097152
 /* The served loop cuts long regions into tiles of this size, whatever the
  * process-wide tiling: a region is spread over more CTAs, which shortens its
- * latency (measured on GB300 at 50 k regions/s: p50 85 -> 66 us, p99 184 ->
- * 153 us against 2 MiB tiles) at a small cost in batch throughput. */
-#define ACCR_SERVED_TILE_BYTES 1048576
+ * latency (measured on GB300 at 50 k regions/s: p50 67 us, p99 160 us, against
+ * 134 / 277 us with 2 MiB tiles) at a small cost in batch throughput. */
+#define ACCR_SERVED_TILE_BYTES 524288
 
 /* ---- patterns of the paper's applications (Sec. 4.2) -------------------------- */
 

@@ -38,7 +38,7 @@ int reduce_grid(int in_type, int nc, int64_t n);
 int reduce_launch(const void *in, int64_t n, int in_type, const ClauseDev *cl, int nc, int two_level,
                   Partial *partials, unsigned *counter, int grid, cudaStream_t s);
 
-constexpr int BB = 512;  // threads per CTA
+constexpr int BB = 256;  // threads per CTA (4 CTAs per SM: one CTA's merge between tiles overlaps the others' streaming)
 constexpr int BU = 4;    // 16-byte vectors per thread per iteration (tiles)
 constexpr int SU = 8;    // 16-byte vectors per lane per iteration (warp regions)
 
@@ -257,7 +257,7 @@ __device__ __noinline__ void warp_fold(const RegionDev *d, int lane) {
     default: FN<double, 2>(__VA_ARGS__); break;                           \
     }
 
-__global__ void __launch_bounds__(BB, 2) batch_kernel(const __grid_constant__ BatchArgs p) {
+__global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ BatchArgs p) {
     __shared__ Acc sh[ACCR_MAX_CLAUSES][BB / 32];
     __shared__ int s_last;
     __shared__ long long s_q;
