@@ -48,33 +48,39 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid barrier for a cooperative launch: generation counting, bounded spin.
-// bar[0] = arrivals, bar[1] = generation.  Returns false if the wait ran out.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &gen) {
+// Grid barrier for a cooperative launch that also ORs one CTA-uniform flag:
+// generation counting, bounded spin.  bar[0] counts arrivals (low 20 bits)
+// and raised flags (bits 20 and up); bar[1] holds (generation << 1) | OR of
+// the flags, published by the last CTA to arrive, so the flag comes back
+// with the release instead of through a word of its own.  Returns 0 if the
+// wait ran out, else 1 + the OR of the flags.
+__device__ __forceinline__ int grid_barrier_or(unsigned *bar, unsigned &gen, bool flag) {
+    __shared__ int s_res;
     __syncthreads();
-    bool ok = true;
     if (threadIdx.x == 0) {
-        const unsigned my = gen + 1;
+        const unsigned my = (gen + 1) & 0x7fffffffu;
         __threadfence();
-        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+        const unsigned old = atomicAdd(&bar[0], 1u + (flag ? (1u << 20) : 0u));
+        int res = 0;
+        if ((old & 0xfffffu) == gridDim.x - 1) {
+            const unsigned any = ((old >> 20) != 0u || flag) ? 1u : 0u;
             bar[0] = 0u;
-            st_release(&bar[1], my);
+            st_release(&bar[1], (my << 1) | any);
+            res = 1 + (int)any;
         } else {
             uint32_t i = 0;
-            while (ld_acquire(&bar[1]) != my) {
-                if (++i > kSpinLimit) {
-                    ok = false;
-                    break;
-                }
+            unsigned v = ld_acquire(&bar[1]);
+            while ((v >> 1) != my && ++i <= kSpinLimit) {
                 __nanosleep(64);
+                v = ld_acquire(&bar[1]);
             }
+            if ((v >> 1) == my) res = 1 + (int)(v & 1u);
         }
+        s_res = res;
     }
-    gen += 1;
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) s_ok = ok;
+    gen = (gen + 1) & 0x7fffffffu;
     __syncthreads();
-    return s_ok != 0;
+    return s_res;
 }
 
 // ============================================================================
@@ -825,28 +831,24 @@ __global__ void __launch_bounds__(BF_THREADS) bfs_level_kernel(const uint8_t *__
 
 // All levels in one cooperative launch: per level, the || of the changed
 // flags goes to a per-level slot, a bounded grid barrier separates levels.
-// One CTA of BFP_THREADS per SM (fewer arrivals per grid barrier), one
-// barrier per level.  The flag of level L lives in slot L % 3: it is written
-// before barrier L and read after it; block 0 clears slot (L + 1) % 3 during
-// level L, when every CTA has passed barrier L - 1 and so has finished
-// reading that slot (last used by level L - 2), and before anyone can write
-// it (level L + 1, after barrier L).
+// One CTA of BFP_THREADS per SM (fewer arrivals per grid barrier) and one
+// barrier per level, which also carries the level's `||` flag: every CTA
+// learns whether any cell changed from the barrier's release itself.
 __global__ void __launch_bounds__(BFP_THREADS, 1) bfs_persistent_kernel(const uint8_t *__restrict__ open, int32_t *dist,
-                                                                       int64_t rows, int64_t cols, unsigned *flags,
+                                                                       int64_t rows, int64_t cols,
                                                                        int64_t max_levels, unsigned *bar,
                                                                        int64_t *levels_out, int *err) {
-    unsigned gen = *(volatile unsigned *)&bar[1];
+    unsigned gen = (*(volatile unsigned *)&bar[1]) >> 1;
     int64_t L = 0;
     for (; L < max_levels; ++L) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(L + 1) % 3] = 0u;
         const bool changed = bfs_level(open, dist, rows, cols, (int32_t)L);
         const int any = __syncthreads_or(changed ? 1 : 0);
-        if (threadIdx.x == 0 && any) atomicOr(&flags[L % 3], 1u);
-        if (!grid_barrier(bar, gen)) {
+        const int r = grid_barrier_or(bar, gen, any != 0);
+        if (r == 0) {
             if (threadIdx.x == 0) atomicExch(err, 7);
             return;
         }
-        if (!*(volatile unsigned *)&flags[L % 3]) break;
+        if (r == 1) break;  // no cell changed at this level
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *levels_out = L + 1;  // the level that found nothing new
 }
@@ -1011,7 +1013,6 @@ extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t
     if (!scr) return ACCR_ENOMEM;
     unsigned *more = scr->counters + 8;
     unsigned *counter = scr->counters + 9;
-    unsigned *flags3 = scr->counters + 16;   // three level slots (persistent form)
     unsigned *bar = scr->counters + 12;      // arrivals, generation
     int *err = (int *)(scr->counters + 14);
     int64_t *lv = (int64_t *)((char *)scr->buf);
@@ -1020,11 +1021,10 @@ extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t
     if (!hmore) return ACCR_ENOMEM;
     if (mode == ACCR_BFS_PERSISTENT) {
         rc = cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "accr_grid_bfs: clear status");
-        if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(flags3, 0, 3 * sizeof(unsigned), s), "accr_grid_bfs: flags");
         if (rc == ACCR_OK) rc = cuda_check(cudaMemsetAsync(bar, 0, sizeof(unsigned), s), "accr_grid_bfs: barrier");
         if (rc != ACCR_OK) return rc;
         int64_t maxl = total + 1;
-        void *args[] = {(void *)&open, (void *)&dist, (void *)&rows, (void *)&cols, (void *)&flags3, (void *)&maxl,
+        void *args[] = {(void *)&open, (void *)&dist, (void *)&rows, (void *)&cols, (void *)&maxl,
                         (void *)&bar, (void *)&lv, (void *)&err};
         if ((rc = launch_guard("bfs_persistent_kernel")) != ACCR_OK) return rc;
         const int pgrid = (int)std::min<int64_t>((total + BFP_THREADS - 1) / BFP_THREADS, (int64_t)di.sms);
