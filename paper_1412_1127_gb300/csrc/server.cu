@@ -49,8 +49,7 @@ struct Slot {
     cudaEvent_t done = nullptr;
     bool busy = false;
     std::vector<Req> reqs;
-    uint64_t *host_res = nullptr;  // pinned, max_batch * ACCR_MAX_CLAUSES
-    uint64_t *dev_res = nullptr;   // device, same size
+    uint64_t *host_res = nullptr;  // pinned, max_batch * ACCR_MAX_CLAUSES; the kernel writes it
     int64_t launch_ns = 0;
     int64_t bytes = 0;
     int status = ACCR_OK;
@@ -146,14 +145,12 @@ int accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
     std::vector<accr_region> regs(s.reqs.size());
     for (size_t i = 0; i < s.reqs.size(); ++i) {
         regs[i] = s.reqs[i].region;
-        for (int c = 0; c < regs[i].nclauses; ++c) regs[i].clauses[c].out = &s.dev_res[i * ACCR_MAX_CLAUSES + c];
+        // the kernel stores each variable straight into the pinned result slots
+        // (no device-to-host copy in the batch's critical path)
+        for (int c = 0; c < regs[i].nclauses; ++c) regs[i].clauses[c].out = &s.host_res[i * ACCR_MAX_CLAUSES + c];
     }
     s.launch_ns = now_ns();
     int rc = batch_launch_regions(regs.data(), (int64_t)regs.size(), (accr_stream_t)s.stream, ACCR_SERVED_TILE_BYTES);
-    if (rc == ACCR_OK)
-        rc = cuda_check(cudaMemcpyAsync(s.host_res, s.dev_res, sizeof(uint64_t) * ACCR_MAX_CLAUSES * regs.size(),
-                                        cudaMemcpyDeviceToHost, s.stream),
-                        "server: results");
     if (rc == ACCR_OK) rc = cuda_check(cudaEventRecord(s.done, s.stream), "server: event");
     s.status = rc;
     lk.lock();
@@ -220,7 +217,6 @@ extern "C" ACCR_API int accr_server_create(uint64_t budget, int32_t nstreams, in
         int rc = cuda_check(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "server: stream");
         if (rc == ACCR_OK) rc = cuda_check(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming), "server: event");
         if (rc == ACCR_OK) rc = cuda_check(cudaMallocHost(&s.host_res, rb), "server: pinned results");
-        if (rc == ACCR_OK) rc = cuda_check(cudaMalloc(&s.dev_res, rb), "server: device results");
         if (rc != ACCR_OK) {
             accr_server_destroy(S);
             return rc;
@@ -288,7 +284,6 @@ extern "C" ACCR_API int accr_server_destroy(accr_server *S) {
         if (s.stream) cudaStreamSynchronize(s.stream);
         if (s.done) cudaEventDestroy(s.done);
         if (s.host_res) cudaFreeHost(s.host_res);
-        if (s.dev_res) cudaFree(s.dev_res);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
     delete S;
