@@ -270,8 +270,8 @@ ACCR_API int accr_batch_tiling(int64_t small_bytes, int64_t tile_bytes,
 #define ACCR_TILE_BYTES 2097152
 /* The served loop cuts long regions into tiles of this size, whatever the
  * process-wide tiling: a region is spread over more CTAs, which shortens its
- * latency (measured on GB300 at 50 k regions/s: p50 67 us, p99 160 us, against
- * 134 / 277 us with 2 MiB tiles) at a small cost in batch throughput. */
+ * latency (measured on GB300 at 50 k regions/s: about half the p50 and p99 of
+ * 2 MiB tiles) at a small cost in batch throughput. */
 #define ACCR_SERVED_TILE_BYTES 524288
 
 /* ---- patterns of the paper's applications (Sec. 4.2) -------------------------- */

@@ -257,7 +257,8 @@ __device__ __noinline__ void warp_fold(const RegionDev *d, int lane) {
     default: FN<double, 2>(__VA_ARGS__); break;                           \
     }
 
-__global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ BatchArgs p) {
+__device__ __forceinline__ void batch_body(const BatchArgs &p, const RegionDev *regions, const int2 *tiles,
+                                           const int32_t *small) {
     __shared__ Acc sh[ACCR_MAX_CLAUSES][BB / 32];
     __shared__ int s_last;
     __shared__ long long s_q;
@@ -270,8 +271,8 @@ __global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ Ba
     __syncthreads();
     while (q < p.T) {
         if (threadIdx.x == 0) s_q = (long long)atomicAdd(&p.queue[0], 1u);
-        const int2 tk = p.tiles[q];
-        const RegionDev *d = p.regions + tk.x;
+        const int2 tk = tiles[q];
+        const RegionDev *d = regions + tk.x;
         const int type = d->in_type, nc = d->nc;
         ACCR_DISPATCH_TYPE_NC(type, nc, tile_fold, p, d, tk.x, (int64_t)tk.y, sh, &s_last);
         __syncthreads();
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ Ba
     while (s < p.S) {
         long long nx = 0;
         if (lane == 0) nx = (long long)atomicAdd(&p.queue[1], 1u);
-        const RegionDev *d = p.regions + p.small[s];
+        const RegionDev *d = regions + small[s];
         const int type = d->in_type, nc = d->nc;
         ACCR_DISPATCH_TYPE_NC(type, nc, warp_fold, d, lane);
         s = __shfl_sync(0xffffffffu, nx, 0);
@@ -301,6 +302,26 @@ __global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ Ba
             p.queue[2] = 0u;
         }
     }
+}
+
+__global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ BatchArgs p) {
+    batch_body(p, p.regions, p.tiles, p.small);
+}
+
+// A small plan (a batch of a few regions, as the served loop forms) travels
+// in the kernel's parameters instead of through a host-to-device copy ahead
+// of the launch; the descriptors are read from the parameter space.
+constexpr int INL_REGIONS = 16, INL_TILES = 1024, INL_SMALL = 16;
+struct BatchArgsInline {
+    BatchArgs b;  // its plan pointers are unused
+    RegionDev regions[INL_REGIONS];
+    int2 tiles[INL_TILES];
+    int32_t small[INL_SMALL];
+};
+static_assert(sizeof(BatchArgsInline) < 32000, "kernel parameters are limited to 32764 bytes");
+
+__global__ void __launch_bounds__(BB, 4) batch_kernel_inline(const __grid_constant__ BatchArgsInline p) {
+    batch_body(p.b, p.regions, p.tiles, p.small);
 }
 
 // ---- host: plans -------------------------------------------------------------------
@@ -571,6 +592,26 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
             if (rc != ACCR_OK) return rc;
             B->ncounters = want;
         }
+    }
+    if (R <= (size_t)INL_REGIONS && P.tiles.size() <= (size_t)INL_TILES && P.small.size() <= (size_t)INL_SMALL) {
+        static BatchArgsInline ai;  // built under B->mu; launched by value
+        static std::mutex inl_mu;
+        std::lock_guard<std::mutex> il(inl_mu);
+        ai.b = args_for(P, B->dev, B->counters);
+        ai.b.regions = nullptr;
+        ai.b.tiles = nullptr;
+        ai.b.small = nullptr;
+        ai.b.partials = (Partial *)B->dev;  // the partial slots start the device buffer
+        std::copy(P.regions.begin(), P.regions.end(), ai.regions);
+        std::copy(P.tiles.begin(), P.tiles.end(), ai.tiles);
+        std::copy(P.small.begin(), P.small.end(), ai.small);
+        int rc = launch_guard("batch_kernel");
+        if (rc != ACCR_OK) return rc;
+        batch_kernel_inline<<<batch_grid(P), BB, 0, s>>>(ai);
+        rc = launched("batch_kernel");
+        if (rc != ACCR_OK) return rc;
+        if (flags & ACCR_SYNC) return cuda_check(cudaStreamSynchronize(s), "batch: sync");
+        return ACCR_OK;
     }
     // pinned staging (double-buffered; wait until the copy that last used it is done)
     const int i = B->next;
