@@ -295,7 +295,7 @@ REDUCE_PAIRS = [  # (element type, sum variable, flags) of the fixed-code two-cl
 @pytest.mark.parametrize("t,acc,flags", REDUCE_PAIRS)
 @pytest.mark.parametrize("ext", ["max", "min"])
 @pytest.mark.parametrize("sum_first", [True, False])
-@pytest.mark.parametrize("n", [1, 33, 65536 + 7, (1 << 20) + 3])
+@pytest.mark.parametrize("n", [0, 1, 33, 65536 + 7, (1 << 20) + 3])
 @pytest.mark.parametrize("two_level", [False, True])
 def test_sum_and_extreme_pairs(t, acc, flags, ext, sum_first, n, two_level):
     """reduction(+:s) reduction(max|min:m) in one pass, in either clause order,
