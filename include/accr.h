@@ -214,8 +214,10 @@ typedef struct accr_batch accr_batch;
  * whole by one warp; a longer region is cut into tiles of ACCR_TILE_BYTES (by
  * default) that CTAs fold independently; the last tile of a region to finish
  * merges the region's tile partials in tile order and writes its variables.
- * The split depends only on each region's own type and length, so a region
- * gives the same bits alone and inside any batch.  A region with three or
+ * The split depends only on each region's own type and length (under the
+ * tiling in force), so a region gives the same bits alone and inside any
+ * batch.  A batch of at most 16 regions passes its plan in the kernel's
+ * arguments; a larger one uploads it with one copy.  A region with three or
  * four clauses is run as two halves (clauses 0-1, 2-3) that each read its
  * elements.
  *
@@ -281,6 +283,10 @@ ACCR_API int accr_batch_tiling(int64_t small_bytes, int64_t tile_bytes,
  * (qx, qy).  d_i = (x_i - qx)^2 + (y_i - qy)^2 in float, every operation
  * rounded (no fused multiply-add); the k smallest by (d, i), ties by index,
  * in increasing order -- a reduction whose operator keeps a sorted list.
+ * For n >= 2^22 a first small launch takes the k-th smallest distance of a
+ * 65,536-point sample as a bound (k real points lie within it), so the scan
+ * launch tests only points within the bound one by one; results do not
+ * depend on it.
  *
  *   pts       DEVICE, n points as float pairs (x0, y0, x1, y1, ...), 8-byte aligned
  *   idx_out   DEVICE int64[k]; d2_out DEVICE float[k] (-1 / +inf past n)
