@@ -5,8 +5,8 @@
 //    reduction whose operator keeps a sorted list of k (distance, index)
 //    pairs.  Each warp keeps one list in shared memory and tests a whole round
 //    of its points against the list's k-th distance at once; a distance bound
-//    taken from a sample of the points first (a separate small launch) keeps
-//    the lists' slow path rare.  The CTA ranks its warps' entries, and the
+//    taken from a sample of the points at the start of the (cooperative)
+//    launch keeps the lists' slow path rare.  The CTA ranks its warps' entries, and the
 //    last CTA to finish merges the CTA lists.
 //
 //  * SRAD: a reduction region whose result feeds a data-parallel region.  The
@@ -285,24 +285,128 @@ __device__ __noinline__ void final_lists(const PairSlot *partials, int64_t nc, f
         }
 }
 
-// bound (nullable, device): a distance that at least k of the points reach
-// (the k-th smallest distance of a sample of them).  Every list starts as KT
-// placeholders (bound, no index), so only points with d <= bound are ever
-// tested in the slow path; since k real points lie within the bound, the
-// placeholders never reach the output.
+// The bound: the first NK_BOUND_CTAS CTAs of the scan launch each take a
+// share of a sample (NK_CHUNKS chunks of NK_CHUNK consecutive points, spread
+// evenly over the array: chunk c starts at point c * stride) and every warp
+// records the smallest distance of its share; those minima belong to
+// distinct points, so the k-th smallest of them is a distance that at least
+// k points reach.  The last sampling CTA selects it and publishes it; every
+// CTA waits for it (bounded: if the wait runs out, the scan proceeds without
+// a bound, which changes its speed, not its result).
+constexpr int NK_CHUNK = 512, NK_CHUNKS = 128, NK_BOUND_CTAS = 64;
+constexpr int NK_BOUND_WARPS = NK_BOUND_CTAS * (NK_THREADS / 32);  // 512 minima
+constexpr int64_t NK_BOUND_MIN_N = 1 << 22;  // smaller inputs skip the bound
+constexpr int NK_BOUND_PER_THREAD = NK_CHUNK * (NK_CHUNKS / NK_BOUND_CTAS) / NK_THREADS;
+constexpr uint32_t kBoundSpin = 1u << 20;    // polls of the published bound (~0.1 s)
+
+template <int KT>
+__device__ __forceinline__ void flist_insert(float (&D)[KT], float d) {
+    if (!(d < D[KT - 1])) return;  // NaN never enters
+#pragma unroll
+    for (int j = KT - 1; j > 0; --j) D[j] = d < D[j - 1] ? D[j - 1] : (d < D[j] ? d : D[j]);
+    D[0] = d < D[0] ? d : D[0];
+}
+
+// Warp minima of this CTA's share of the sample (one per warp, to minima[]).
+__device__ __forceinline__ void sample_minima(const float2 *__restrict__ pts, int64_t stride, float qx, float qy,
+                                              float *minima) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 v[NK_BOUND_PER_THREAD];
+#pragma unroll
+    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) {  // every load first
+        const int t = e * NK_THREADS + threadIdx.x;   // point t of this CTA's chunks
+        const int c = blockIdx.x * (NK_CHUNKS / NK_BOUND_CTAS) + t / NK_CHUNK;
+        v[e] = __ldg(pts + (int64_t)c * stride + (t % NK_CHUNK));
+    }
+    float m = INFINITY;  // fminf passes over NaN distances
+#pragma unroll
+    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) m = fminf(m, sqdist(v[e].x, v[e].y, qx, qy));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) minima[blockIdx.x * (NK_THREADS / 32) + warp] = m;
+}
+
+// The k-th smallest of the NK_BOUND_WARPS minima (one warp; every lane gets it).
+template <int KT>
+__device__ __forceinline__ float kth_of_minima(const float *minima, int k) {
+    const int lane = threadIdx.x & 31;
+    constexpr int PER_LANE = NK_BOUND_WARPS / 32;
+    float D[KT], mv[PER_LANE];
+#pragma unroll
+    for (int j = 0; j < KT; ++j) D[j] = INFINITY;
+#pragma unroll
+    for (int j = 0; j < PER_LANE; ++j) mv[j] = __ldcg(minima + j * 32 + lane);  // all loads in flight
+#pragma unroll
+    for (int j = 0; j < PER_LANE; ++j) flist_insert<KT>(D, mv[j]);
+    // k rounds of a warp minimum, each taking the head of exactly one lane
+    float t = INFINITY;
+    for (int r = 0; r < k; ++r) {
+        float w = D[0];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
+        t = w;
+        const unsigned who = __ballot_sync(0xffffffffu, D[0] == w);
+        if (lane == __ffs(who) - 1) {
+#pragma unroll
+            for (int j = 0; j < KT - 1; ++j) D[j] = D[j + 1];
+            D[KT - 1] = INFINITY;
+        }
+    }
+    return t;
+}
+
+// With sample_stride > 0 (a cooperative launch of at least NK_BOUND_CTAS
+// CTAs) the kernel first takes the sampled bound T: every list starts as KT
+// placeholders (T, no index), so only points with d <= T are ever tested in
+// the slow path; since k real points lie within T, the placeholders never
+// reach the output.  bstate[0..2]: sampling CTAs arrived, bound published,
+// bound bits; zero on entry and exit.
 template <int KT, int NT>
 __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
                                                      int k, int64_t *idx_out, float *d_out, PairSlot *partials,
-                                                     unsigned *counter, const float *bound) {
+                                                     unsigned *counter, int64_t sample_stride, float *minima,
+                                                     unsigned *bstate) {
     __shared__ float wld[NT / 32][KT];
     __shared__ int64_t wli[NT / 32][KT];
     __shared__ float MD[KT];
     __shared__ int64_t MI[KT];
     __shared__ int am_last;
+    __shared__ float s_T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *LD = wld[warp];
     int64_t *LI = wli[warp];
-    const float T = bound ? __ldg(bound) : INFINITY;
+    float T = INFINITY;
+    if (sample_stride > 0) {
+        if (blockIdx.x < NK_BOUND_CTAS) {
+            sample_minima((const float2 *)pts, sample_stride, qx, qy, minima);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                am_last = atomicAdd(&bstate[0], 1u) == (unsigned)NK_BOUND_CTAS - 1u;
+            }
+            __syncthreads();
+            if (am_last && warp == 0) {
+                __threadfence();
+                const float t = kth_of_minima<KT>(minima, k);
+                if (lane == 0) {
+                    bstate[2] = __float_as_uint(t);
+                    __threadfence();
+                    st_release(&bstate[1], 1u);
+                }
+            }
+        }
+        if (threadIdx.x == 0) {  // every CTA waits for the bound, a bounded number of polls
+            uint32_t i = 0;
+            unsigned f = ld_acquire(&bstate[1]);
+            while (f == 0u && ++i <= kBoundSpin) {
+                __nanosleep(64);
+                f = ld_acquire(&bstate[1]);
+            }
+            s_T = f ? __uint_as_float(*(volatile unsigned *)&bstate[2]) : INFINITY;
+        }
+        __syncthreads();
+        T = s_T;
+    }
     if (lane < KT) {
         LD[lane] = T;
         LI[lane] = INT64_MAX;
@@ -396,91 +500,11 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
             d_out[j] = real ? MD[j] : INFINITY;
         }
         *counter = 0u;
-    }
-}
-
-// The bound: each warp of NK_BOUND_CTAS CTAs takes the smallest distance of
-// its share of a sample (NK_CHUNKS chunks of NK_CHUNK consecutive points,
-// spread evenly over the array: chunk c starts at point c * stride); those
-// minima belong to distinct points, so the k-th smallest of them is a
-// distance that at least k points reach.  The last CTA to finish selects it.
-constexpr int NK_CHUNK = 512, NK_CHUNKS = 128, NK_BOUND_CTAS = 64;
-constexpr int NK_BOUND_WARPS = NK_BOUND_CTAS * (NK_THREADS / 32);  // 512 minima
-constexpr int64_t NK_BOUND_MIN_N = 1 << 22;  // smaller inputs skip the bound (its launch costs more)
-constexpr int NK_BOUND_PER_THREAD = NK_CHUNK * (NK_CHUNKS / NK_BOUND_CTAS) / NK_THREADS;
-
-template <int KT>
-__device__ __forceinline__ void flist_insert(float (&D)[KT], float d) {
-    if (!(d < D[KT - 1])) return;  // NaN never enters
-#pragma unroll
-    for (int j = KT - 1; j > 0; --j) D[j] = d < D[j - 1] ? D[j - 1] : (d < D[j] ? d : D[j]);
-    D[0] = d < D[0] ? d : D[0];
-}
-
-template <int KT>
-__global__ void __launch_bounds__(NK_THREADS) nearest_bound_kernel(const float2 *__restrict__ pts, int64_t stride,
-                                                                    float qx, float qy, int k, float *minima,
-                                                                    unsigned *counter, float *bound) {
-    __shared__ int am_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 v[NK_BOUND_PER_THREAD];
-#pragma unroll
-    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) {  // every load first
-        const int t = e * NK_THREADS + threadIdx.x;   // point t of this CTA's chunks
-        const int c = blockIdx.x * (NK_CHUNKS / NK_BOUND_CTAS) + t / NK_CHUNK;
-        v[e] = __ldg(pts + (int64_t)c * stride + (t % NK_CHUNK));
-    }
-    float m = INFINITY;  // fminf passes over NaN distances
-#pragma unroll
-    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) m = fminf(m, sqdist(v[e].x, v[e].y, qx, qy));
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) minima[blockIdx.x * (NK_THREADS / 32) + warp] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        am_last = atomicAdd(counter, 1u) == (unsigned)gridDim.x - 1u;
-    }
-    __syncthreads();
-    if (!am_last || warp != 0) return;
-    __threadfence();
-    float D[KT];
-#pragma unroll
-    for (int j = 0; j < KT; ++j) D[j] = INFINITY;
-    constexpr int PER_LANE = NK_BOUND_WARPS / 32;
-    float mv[PER_LANE];
-#pragma unroll
-    for (int j = 0; j < PER_LANE; ++j) mv[j] = __ldcg(minima + j * 32 + lane);  // all loads in flight
-#pragma unroll
-    for (int j = 0; j < PER_LANE; ++j) flist_insert<KT>(D, mv[j]);
-    // the k-th smallest of the 32 lanes' ascending lists: k rounds of a warp
-    // minimum, each taking the head of exactly one lane
-    float t = INFINITY;
-    for (int r = 0; r < k; ++r) {
-        float w = D[0];
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
-        t = w;
-        const unsigned who = __ballot_sync(0xffffffffu, D[0] == w);
-        if (lane == __ffs(who) - 1) {
-#pragma unroll
-            for (int j = 0; j < KT - 1; ++j) D[j] = D[j + 1];
-            D[KT - 1] = INFINITY;
+        if (sample_stride > 0) {  // every CTA read the bound before its scan
+            bstate[0] = 0u;
+            bstate[1] = 0u;
         }
     }
-    if (lane == 0) {
-        *bound = t;
-        *counter = 0u;
-    }
-}
-
-template <int KT>
-static int nearest_one(const float *pts, int64_t n, float qx, float qy, int k, int64_t *idx, float *d,
-                       PairSlot *partials, unsigned *counter, const float *bound, int grid, cudaStream_t s) {
-    int rc = launch_guard("nearest_kernel");
-    if (rc != ACCR_OK) return rc;
-    nearest_kernel<KT, NK_THREADS><<<grid, NK_THREADS, 0, s>>>(pts, n, qx, qy, k, idx, d, partials, counter, bound);
-    return launched("nearest_kernel");
 }
 
 template <int KT>
@@ -494,31 +518,33 @@ static int nearest_launch(const float *pts, int64_t n, float qx, float qy, int k
         if (per_sm < 1) per_sm = 1;
     });
     const DeviceInfo &di = device_info();
-    auto grid_for = [&](int64_t m) {
-        const int64_t want = (m / 2 + NT * 16 - 1) / (NT * 16);  // one round of 16 vectors per thread
-        return (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
-    };
-    const int grid = grid_for(n);
-    const bool use_bound = n >= NK_BOUND_MIN_N;
-    // scratch: [partials: grid * KT slots][the sample's warp minima][the bound]
+    const int64_t want = (n / 2 + NT * 16 - 1) / (NT * 16);  // one round of 16 vectors per thread
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
+    // the bound needs its sampling CTAs resident with the others: a cooperative launch
+    const bool use_bound = n >= NK_BOUND_MIN_N && grid >= NK_BOUND_CTAS;
+    // scratch: [partials: grid * KT slots][the sample's warp minima]
     const size_t part_bytes = sizeof(PairSlot) * (size_t)grid * KT;
-    const size_t lists_off = (part_bytes + 255) & ~(size_t)255;
-    const size_t bound_off = lists_off + sizeof(float) * NK_BOUND_WARPS;
-    Scratch *scr = scratch_for((accr_stream_t)s, use_bound ? bound_off + 16 : part_bytes);
+    const size_t minima_off = (part_bytes + 255) & ~(size_t)255;
+    Scratch *scr = scratch_for((accr_stream_t)s, minima_off + sizeof(float) * NK_BOUND_WARPS);
     if (!scr) return ACCR_ENOMEM;
     PairSlot *partials = (PairSlot *)scr->buf;
-    const float *bound = nullptr;
-    int rc;
+    unsigned *counter = scr->counters + 1;
+    unsigned *bstate = scr->counters + 5;  // words 5-7
+    float *minima = (float *)((char *)scr->buf + minima_off);
+    int64_t stride = use_bound ? n / NK_CHUNKS : 0;
+    int rc = launch_guard("nearest_kernel");
+    if (rc != ACCR_OK) return rc;
     if (use_bound) {
-        char *b = (char *)scr->buf;
-        float *bnd = (float *)(b + bound_off);
-        if ((rc = launch_guard("nearest_bound_kernel")) != ACCR_OK) return rc;
-        nearest_bound_kernel<KT><<<NK_BOUND_CTAS, NT, 0, s>>>((const float2 *)pts, n / NK_CHUNKS, qx, qy, k,
-                                                             (float *)(b + lists_off), scr->counters + 5, bnd);
-        if ((rc = launched("nearest_bound_kernel")) != ACCR_OK) return rc;
-        bound = bnd;
+        void *args[] = {(void *)&pts, (void *)&n, (void *)&qx, (void *)&qy, (void *)&k, (void *)&idx, (void *)&d,
+                        (void *)&partials, (void *)&counter, (void *)&stride, (void *)&minima, (void *)&bstate};
+        rc = cuda_check(cudaLaunchCooperativeKernel((const void *)nearest_kernel<KT, NT>, grid, NT, args, 0, s),
+                        "accr_nearest_k: cooperative launch");
+        if (rc != ACCR_OK) return rc;
+    } else {
+        nearest_kernel<KT, NT><<<grid, NT, 0, s>>>(pts, n, qx, qy, k, idx, d, partials, counter, stride, minima,
+                                                    bstate);
     }
-    return nearest_one<KT>(pts, n, qx, qy, k, idx, d, partials, scr->counters + 1, bound, grid, s);
+    return launched("nearest_kernel");
 }
 
 // ============================================================================
