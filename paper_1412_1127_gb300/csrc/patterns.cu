@@ -671,6 +671,11 @@ __device__ __forceinline__ void publish_stats(const StdArgs &p, const StatPartia
     (void)sh;
 }
 
+// SU vectors in flight per thread; a group's loads all come before its
+// stores (each element is read and written by the same thread, so the order
+// is right even when y aliases x).  The separate elementwise launch gains from
+// four; inside the fused launch one is faster.
+template <int SU>
 __device__ __forceinline__ void map_pass(const float *x, float *y, int64_t n, float mean_f, float rstd_f) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -679,7 +684,21 @@ __device__ __forceinline__ void map_pass(const float *x, float *y, int64_t n, fl
         const int64_t nv = n / 4;
         const float4 *x4 = (const float4 *)x;
         float4 *y4 = (float4 *)y;
-        for (int64_t v = gtid; v < nv; v += nth) {
+        int64_t v = gtid;
+        for (; v + (SU - 1) * nth < nv; v += SU * nth) {
+            float4 a[SU];
+#pragma unroll
+            for (int u = 0; u < SU; ++u) a[u] = x4[v + u * nth];
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+                a[u].x = __fmul_rn(__fsub_rn(a[u].x, mean_f), rstd_f);
+                a[u].y = __fmul_rn(__fsub_rn(a[u].y, mean_f), rstd_f);
+                a[u].z = __fmul_rn(__fsub_rn(a[u].z, mean_f), rstd_f);
+                a[u].w = __fmul_rn(__fsub_rn(a[u].w, mean_f), rstd_f);
+                y4[v + u * nth] = a[u];
+            }
+        }
+        for (; v < nv; v += nth) {
             float4 a = x4[v];
             a.x = __fmul_rn(__fsub_rn(a.x, mean_f), rstd_f);
             a.y = __fmul_rn(__fsub_rn(a.y, mean_f), rstd_f);
@@ -759,7 +778,7 @@ __global__ void __launch_bounds__(SD_THREADS) standardize_kernel(const __grid_co
     __threadfence();
     const float mean_f = *(volatile float *)&p.shared->mean_f;
     const float rstd_f = *(volatile float *)&p.shared->rstd_f;
-    map_pass(p.x, p.y, p.n, mean_f, rstd_f);
+    map_pass<1>(p.x, p.y, p.n, mean_f, rstd_f);
 }
 
 __global__ void map_kernel(const float *x, float *y, int64_t n, const StdShared *st, float mean_f, float rstd_f,
@@ -768,7 +787,7 @@ __global__ void map_kernel(const float *x, float *y, int64_t n, const StdShared 
         mean_f = st->mean_f;
         rstd_f = st->rstd_f;
     }
-    map_pass(x, y, n, mean_f, rstd_f);
+    map_pass<4>(x, y, n, mean_f, rstd_f);
 }
 
 // ============================================================================
