@@ -54,3 +54,18 @@ def test_bfs_fixture_satisfies_the_level_equations():
     assert levels == dist.max() + 1
     od, ol = oracle.grid_bfs(grid, src)
     assert np.array_equal(od, dist) and ol == levels
+
+
+def test_fixtures_are_what_the_writer_produces(tmp_path, monkeypatch):
+    """The stored files are exactly what tests/golden/make_golden.py writes
+    from the oracle and the closed form (so no stored value has another source)."""
+    import os
+    import make_golden
+    monkeypatch.setattr(make_golden, "HERE", str(tmp_path))
+    make_golden.write_reduce()
+    make_golden.write_listing1()
+    make_golden.write_nearest()
+    make_golden.write_bfs()
+    for name in sorted(os.listdir(tmp_path)):
+        with open(os.path.join(tmp_path, name)) as a, open(os.path.join(G.HERE, name)) as b:
+            assert a.read() == b.read(), name
