@@ -1,0 +1,63 @@
+"""Host-side logic that needs no GPU: the bench's traffic record and source
+hash, the autotuner's table, and the library's process-wide batch tiling."""
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+from paper_1412_1127_gb300 import api, autotune
+
+REDUCE_SOURCES = ["paper_1412_1127_gb300/csrc/reduce.cu", "paper_1412_1127_gb300/csrc/fold.cuh"]
+
+
+def test_committed_traffic_record_matches_the_current_kernel():
+    """profiles/traffic.txt carries the hash of the reduce kernel it was taken
+    on; it must be the current one (else bench.py reports traffic as null)."""
+    assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is not None
+
+
+def test_traffic_record_is_dropped_when_the_kernel_changes(tmp_path, monkeypatch):
+    root = tmp_path / "repo"
+    for f in REDUCE_SOURCES:
+        os.makedirs(root / os.path.dirname(f), exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, f), root / f)
+    os.makedirs(root / "profiles")
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.txt"), root / "profiles" / "traffic.txt")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is not None
+    # a change before the first kernel (host-side) keeps the hash ...
+    src = root / REDUCE_SOURCES[0]
+    text = src.read_text()
+    src.write_text("// host-side note\n" + text)
+    assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is not None
+    # ... a change inside the device code drops the record
+    i = text.index("__global__") + len("__global__")
+    src.write_text(text[:i] + " /* changed */" + text[i:])
+    assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is None
+    assert bench.ncu_traffic("no_such_kernel", "scalar_2^28", REDUCE_SOURCES) is None
+
+
+def test_whole_job_rate_counts_every_rank():
+    assert bench.whole_job_rate(10.0, 4, 2.0) == pytest.approx(20.0)
+
+
+def test_autotune_table_roundtrip_and_apply(tmp_path):
+    old = api.accr_batch_tiling()
+    try:
+        p = str(tmp_path / "t.json")
+        d = autotune.save(32768, 1048576, {(32768, 1048576): 1.25, (65536, 2097152): 1.5}, path=p, note="x")
+        assert json.load(open(p)) == d
+        got = autotune.load(p)
+        assert (got["small_bytes"], got["tile_bytes"]) == (32768, 1048576)
+        assert tuple(api.accr_batch_tiling()) == (32768, 1048576)
+        assert autotune.load(str(tmp_path / "missing.json")) is None
+    finally:
+        api.accr_batch_tiling(*old)
+
+
+def test_committed_tuning_table_is_consistent():
+    d = json.load(open(autotune.TABLE))
+    assert d["small_bytes"] % 16 == 0 and d["tile_bytes"] % 16 == 0 and d["tile_bytes"] >= 4096
+    assert "%d,%d" % (d["small_bytes"], d["tile_bytes"]) in d["timings_ms"]
