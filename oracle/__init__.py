@@ -42,6 +42,8 @@ class OracleLib:
         L.oracle_matmul_listing1_at.restype = ctypes.c_float
         L.oracle_matmul_truth_at.argtypes = [vp, vp, i64, i64, i64, vp]
         L.oracle_matmul_truth_at.restype = ctypes.c_double
+        L.oracle_matmul_listing1_rows_bt.argtypes = [vp, vp, vp, i64, i64, i64]
+        L.oracle_matmul_truth_rows_bt.argtypes = [vp, vp, vp, vp, i64, i64, i64]
         L.oracle_nearest_k.argtypes = [vp, i64, ctypes.c_float, ctypes.c_float, i, vp, vp]
         L.oracle_standardize.argtypes = [vp, i64, vp, vp]
         L.oracle_grid_bfs.argtypes = [vp, i64, i64, i64, vp]
@@ -142,6 +144,35 @@ class OracleLib:
         c = self.L.oracle_matmul_truth_at(_ptr(a), _ptr(b), n, i, j, _ptr(s))
         return c, s[0]
 
+    def _row_blocks(self, n, fn, threads):
+        import concurrent.futures as cf
+        threads = max(1, min(threads or os.cpu_count() or 1, n or 1))
+        step = -(-n // threads) if n else 1
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:   # ctypes releases the GIL
+            list(ex.map(lambda i0: fn(i0, min(i0 + step, n)), range(0, n, step)))
+
+    def matmul_listing1_threads(self, a, b, threads=None):
+        """matmul_listing1 with rows split over host threads (b read through
+        its transpose); the same bits, each entry computed as Listing 1a does."""
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        bt = np.ascontiguousarray(np.asarray(b, dtype=np.float32).T)
+        n = a.shape[0]
+        c = np.zeros((n, n), dtype=np.float32)
+        self._row_blocks(n, lambda i0, i1: self.L.oracle_matmul_listing1_rows_bt(
+            _ptr(a), _ptr(bt), _ptr(c), n, i0, i1), threads)
+        return c
+
+    def matmul_truth_threads(self, a, b, threads=None):
+        """matmul_truth with rows split over host threads."""
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        bt = np.ascontiguousarray(np.asarray(b, dtype=np.float32).T)
+        n = a.shape[0]
+        c = np.zeros((n, n), dtype=np.float64)
+        s = np.zeros((n, n), dtype=np.float64)
+        self._row_blocks(n, lambda i0, i1: self.L.oracle_matmul_truth_rows_bt(
+            _ptr(a), _ptr(bt), _ptr(c), _ptr(s), n, i0, i1), threads)
+        return c, s
+
 
     def nearest_k(self, pts, qx, qy, k):
         """(idx[k], d2[k]): the k points nearest to (qx, qy) by squared distance,
@@ -229,6 +260,14 @@ def matmul_listing1(a, b):
 
 def matmul_truth(a, b):
     return default().matmul_truth(a, b)
+
+
+def matmul_listing1_threads(a, b, threads=None):
+    return default().matmul_listing1_threads(a, b, threads)
+
+
+def matmul_truth_threads(a, b, threads=None):
+    return default().matmul_truth_threads(a, b, threads)
 
 
 def matmul_listing1_at(a, b, i, j):

@@ -406,6 +406,44 @@ void oracle_matmul_truth(const float *a, const float *b, double *c64,
                 a, b, len, i, j, absab ? &absab[i * len + j] : NULL);
 }
 
+/* Rows i0..i1-1 of the two nests above, with b given through its transpose
+ * (bt[j * len + l] == b[l * len + j]).  The arithmetic and its order are those
+ * of Listing 1a (l ascending, float accumulator rounded after every multiply
+ * and add); only the layout of b differs, so that both operands are read
+ * along memory and independent row blocks of a large product can run in
+ * separate threads. */
+void oracle_matmul_listing1_rows_bt(const float *a, const float *bt, float *c,
+                                    int64_t len, int64_t i0, int64_t i1)
+{
+    int64_t i, j, l;
+    for (i = i0; i < i1; ++i)
+        for (j = 0; j < len; ++j) {
+            const float *ar = a + i * len, *bc = bt + j * len;
+            float sum = 0;
+            for (l = 0; l < len; ++l) sum += ar[l] * bc[l];
+            c[i * len + j] = sum;
+        }
+}
+
+void oracle_matmul_truth_rows_bt(const float *a, const float *bt, double *c64,
+                                 double *absab, int64_t len, int64_t i0,
+                                 int64_t i1)
+{
+    int64_t i, j, l;
+    for (i = i0; i < i1; ++i)
+        for (j = 0; j < len; ++j) {
+            const float *ar = a + i * len, *bc = bt + j * len;
+            double s = 0.0, t = 0.0;
+            for (l = 0; l < len; ++l) {
+                double p = (double)ar[l] * (double)bc[l];
+                s += p;
+                t += fabs(p);
+            }
+            c64[i * len + j] = s;
+            absab[i * len + j] = t;
+        }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Application patterns (Sec. 4.2).                                          */
 /* ------------------------------------------------------------------------- */

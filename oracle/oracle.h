@@ -98,6 +98,16 @@ float oracle_matmul_listing1_at(const float *a, const float *b, int64_t len,
 double oracle_matmul_truth_at(const float *a, const float *b, int64_t len,
                               int64_t i, int64_t j, double *absab);
 
+/* Rows [i0, i1) of the two nests, reading b through its transpose bt
+ * (bt[j*len + l] == b[l*len + j]); same arithmetic in the same order.  The
+ * outputs c / c64 / absab are the full len x len arrays; only rows i0..i1-1
+ * are written. */
+void oracle_matmul_listing1_rows_bt(const float *a, const float *bt, float *c,
+                                    int64_t len, int64_t i0, int64_t i1);
+void oracle_matmul_truth_rows_bt(const float *a, const float *bt, double *c64,
+                                 double *absab, int64_t len, int64_t i0,
+                                 int64_t i1);
+
 /* ---- patterns of the paper's applications (Sec. 4.2) ----------------------- */
 
 /* Nearest Neighbor: squared distances d_i = (x_i-qx)^2 + (y_i-qy)^2 of the n

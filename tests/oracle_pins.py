@@ -360,6 +360,33 @@ def pin_matmul_identity_and_transpose(orc):
     assert t == c64[5, 6] and ts == s[5, 6]
 
 
+
+def pin_matmul_row_blocks(orc):
+    """The threaded row-block form (b read through its transpose): every entry
+    is the sequential float sum of its products (numpy's float32 cumsum adds
+    in index order, rounding each step), ragged row blocks included; the truth
+    form agrees with a float64 product and exact small-integer sums."""
+    g = np.random.default_rng(31)
+    n = 37
+    a = (g.random((n, n)) * 2 - 1).astype(np.float32)
+    b = (g.random((n, n)) * 2 - 1).astype(np.float32)
+    for threads in [1, 3, 8, 64]:
+        c = orc.matmul_listing1_threads(a, b, threads)
+        for i in range(n):
+            prods = (a[i, :][:, None] * b).astype(np.float32)       # prods[l, j]
+            assert np.array_equal(c[i], np.cumsum(prods, axis=0, dtype=np.float32)[-1]), (threads, i)
+        c64, s = orc.matmul_truth_threads(a, b, threads)
+        ref = a.astype(np.float64) @ b.astype(np.float64)
+        assert np.all(np.abs(c64 - ref) <= 1e-13 * s)
+        assert np.allclose(s, np.abs(a).astype(np.float64) @ np.abs(b).astype(np.float64), rtol=1e-13)
+    ai = g.integers(-16, 17, size=(n, n)).astype(np.float32)
+    bi = g.integers(-16, 17, size=(n, n)).astype(np.float32)
+    exact = ai.astype(np.int64) @ bi.astype(np.int64)
+    assert np.array_equal(orc.matmul_listing1_threads(ai, bi, 5), exact.astype(np.float32))
+    c64, s = orc.matmul_truth_threads(ai, bi, 5)
+    assert np.array_equal(c64, exact.astype(np.float64))
+    assert np.array_equal(s, np.abs(ai).astype(np.int64) @ np.abs(bi).astype(np.int64))
+
 # --------------------------------------------------------------------------
 # application patterns (Sec. 4.2): Nearest Neighbor, SRAD, BFS
 # --------------------------------------------------------------------------

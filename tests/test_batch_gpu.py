@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import oracle
+from guard import guarded
 from paper_1412_1127_gb300 import api, inputs
 from tolerances import TOL_F32, TOL_F32_COMP, TOL_F64, same_bits
 
@@ -58,10 +59,10 @@ def test_segmented_int_bit_exact(op, t, acc):
     off = inputs.offsets_from_lengths(L)
     v = values_for(t, int(off[-1]), op, salt=len(op))
     vt = torch.from_numpy(v).cuda()
-    out = torch.full((len(L),), 5, dtype=TD[acc], device="cuda")
-    api.accr_segmented_reduce(vt, off, [api.clause(op, out, init=3)])
+    out = guarded((len(L),), TD[acc], 5)
+    api.accr_segmented_reduce(vt, off, [api.clause(op, out.t, init=3)])
     want = oracle.segmented_reduce(v, off, op, acc, init=3)
-    assert np.array_equal(out.cpu().numpy(), want)
+    assert np.array_equal(out.check("segmented %s" % op).cpu().numpy(), want)
 
 
 @pytest.mark.parametrize("t,acc", [("f32", "f32"), ("f32", "f64"), ("f64", "f64")])
@@ -70,16 +71,14 @@ def test_segmented_fp(t, acc):
     off = inputs.offsets_from_lengths(L)
     v = values_for(t, int(off[-1]), "add", salt=9)
     vt = torch.from_numpy(v).cuda()
-    mx = torch.empty(len(L), dtype=TD[acc], device="cuda")
-    mn = torch.empty(len(L), dtype=TD[acc], device="cuda")
-    s = torch.empty(len(L), dtype=TD[acc], device="cuda")
+    mx, mn, s = (guarded((len(L),), TD[acc]) for _ in range(3))
     flags = api.ACCR_COMPENSATED if (t, acc) == ("f32", "f32") else 0
-    api.accr_segmented_reduce(vt, off, [api.clause("max", mx), api.clause("min", mn), api.clause("add", s)],
-                              flags=flags)
-    assert same_bits(mx.cpu().numpy(), oracle.segmented_reduce(v, off, "max", acc))
-    assert same_bits(mn.cpu().numpy(), oracle.segmented_reduce(v, off, "min", acc))
+    api.accr_segmented_reduce(vt, off, [api.clause("max", mx.t), api.clause("min", mn.t),
+                                        api.clause("add", s.t)], flags=flags)
+    assert same_bits(mx.check("max").cpu().numpy(), oracle.segmented_reduce(v, off, "max", acc))
+    assert same_bits(mn.check("min").cpu().numpy(), oracle.segmented_reduce(v, off, "min", acc))
     tol = TOL_F32_COMP if flags else TOL_F64 if acc == "f64" else TOL_F32
-    s_np = s.cpu().numpy()
+    s_np = s.check("sum").cpu().numpy()
     for k in range(len(L)):
         seg = v[off[k]:off[k + 1]]
         truth = oracle.truth_sum(seg)
@@ -107,18 +106,37 @@ def _mixed_regions(seed=0):
     return specs
 
 
+SLOT_GAP = 3   # untouched elements between neighbouring variables
+
+
 def _run_mixed(specs, subset=None, salt=0):
+    """Runs a batch whose variables are one-element views into one guarded
+    array per variable type, SLOT_GAP elements apart: a store to the wrong
+    slot, or past the last one, changes a sentinel."""
     data, regions, outs = [], [], []
+    arrays = {a: guarded((SLOT_GAP * 4 * len(specs) + SLOT_GAP,), TD[a], 7) for a in TD}
+    used = {a: 0 for a in TD}
     for k, (t, n, cls, fl) in enumerate(specs):
         x = values_for(t, n, "add", salt=salt + k)
         xt = torch.from_numpy(x).cuda()
-        os_ = [torch.full((1,), 7, dtype=TD[a], device="cuda") for _, a in cls]
+        os_ = []
+        for _, a in cls:
+            used[a] += SLOT_GAP
+            os_.append(arrays[a].t[used[a]:used[a] + 1])
         data.append(x)
         outs.append(os_)
         regions.append((xt, [api.clause(op, o, init=1) for (op, _), o in zip(cls, os_)], fl))
     idx = range(len(specs)) if subset is None else subset
     api.accr_batch_reduce([regions[i] for i in idx])
     torch.cuda.synchronize()
+    written = {a: set() for a in TD}
+    for i in idx:
+        for (_, a), o in zip(specs[i][2], outs[i]):
+            written[a].add((o.data_ptr() - arrays[a].t.data_ptr()) // o.element_size())
+    for a, g in arrays.items():
+        vals = g.check("batch variables (%s)" % a).cpu().numpy()
+        others = np.array([j for j in range(vals.size) if j not in written[a]], dtype=np.int64)
+        assert np.all(vals[others] == 7), "a store landed outside its variable (%s)" % a
     return data, {i: [o.cpu().numpy()[0] for o in outs[i]] for i in idx}, regions
 
 
@@ -174,9 +192,9 @@ def test_tiling_changes_keep_results_correct():
     try:
         for small, tile in [(16, 4096), (0, 65536), (1 << 20, 1 << 20), (65536, 131072)]:
             api.accr_batch_tiling(small or 16, tile)
-            out = torch.empty(len(L), dtype=torch.int64, device="cuda")
-            api.accr_segmented_reduce(vt, off, [api.clause("add", out)])
-            assert np.array_equal(out.cpu().numpy(), want), (small, tile)
+            out = guarded((len(L),), torch.int64)
+            api.accr_segmented_reduce(vt, off, [api.clause("add", out.t)])
+            assert np.array_equal(out.check("tiling %d/%d" % (small, tile)).cpu().numpy(), want), (small, tile)
     finally:
         api.accr_batch_tiling(*old)
 
@@ -197,9 +215,8 @@ def test_many_regions_full_size():
     lengths, pf, off_f, pi, off_i = inputs.batched_regions()
     tf, ti = torch.from_numpy(pf).cuda(), torch.from_numpy(pi).cuda()
     nf, ni = len(off_f) - 1, len(off_i) - 1
-    sf = torch.empty(nf, dtype=torch.float32, device="cuda")
-    si = torch.empty(ni, dtype=torch.int64, device="cuda")
-    xi = torch.empty(ni, dtype=torch.int64, device="cuda")
+    gf, gi, gx = guarded((nf,), torch.float32), guarded((ni,), torch.int64), guarded((ni,), torch.int64)
+    sf, si, xi = gf.t, gi.t, gx.t
     regions = []
     for k in range(len(lengths)):
         if k % 2 == 0:
@@ -213,6 +230,7 @@ def test_many_regions_full_size():
     api.accr_batch_reduce(regions)
     torch.cuda.synchronize()
     assert api.accr_launch_count() - before == 1
+    gf.check("float sums"), gi.check("int sums"), gx.check("xors")
     assert np.array_equal(si.cpu().numpy(), oracle.segmented_reduce(pi, off_i, "add", "i64"))
     assert np.array_equal(xi.cpu().numpy(), oracle.segmented_reduce(pi, off_i, "bxor", "i64"))
     s_np = sf.cpu().numpy()

@@ -42,6 +42,11 @@ MUTANTS = [
     ("variance_sign", "var = n > 0 ? s2 / (double)n - mean * mean : 0.0;", "var = n > 0 ? s2 / (double)n + mean * mean : 0.0;"),
     ("bfs_no_left_move", "if (q > 0) nb[cnt++] = u - 1;", ""),
     ("bfs_ignores_walls", "if (open[v] && dist[v] < 0) {", "if (dist[v] < 0) {"),
+    ("rows_bt_reads_b_layout", "for (l = 0; l < len; ++l) sum += ar[l] * bc[l];",
+     "for (l = 0; l < len; ++l) sum += ar[l] * bt[l * len + j];"),
+    ("rows_bt_truth_transposed", "double p = (double)ar[l] * (double)bc[l];",
+     "double p = (double)ar[l] * (double)bt[l * len + j];"),
+    ("rows_bt_abs_is_signed", "absab[i * len + j] = t;", "absab[i * len + j] = s;"),
     ("truth_abs_drops_sign", "la_add(&A, fabs(load_fp(x, in_type, i * stride)));",
      "la_add(&A, load_fp(x, in_type, i * stride));"),
 ]

@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+from guard import guarded
 from paper_1412_1127_gb300 import api, inputs
 
 pytestmark = pytest.mark.gpu
@@ -23,12 +24,11 @@ def test_nearest_k_exact(n, k):
         big = np.zeros((n + off, 2), dtype=np.float32)
         big[off:] = pts
         pt = torch.from_numpy(big).cuda()[off:]
-        idx = torch.empty(k, dtype=torch.int64, device="cuda")
-        d2 = torch.empty(k, dtype=torch.float32, device="cuda")
-        api.accr_nearest_k(pt, qx, qy, k, idx, d2, flags=api.ACCR_SYNC)
+        gi, gd = guarded((k,), torch.int64, -7), guarded((k,), torch.float32, -7)
+        api.accr_nearest_k(pt, qx, qy, k, gi.t, gd.t, flags=api.ACCR_SYNC)
         wi, wd = oracle.nearest_k(pts, qx, qy, k)
-        assert np.array_equal(idx.cpu().numpy(), wi), (n, k, off)
-        assert np.array_equal(d2.cpu().numpy(), wd), (n, k, off)
+        assert np.array_equal(gi.check("idx").cpu().numpy(), wi), (n, k, off)
+        assert np.array_equal(gd.check("d2").cpu().numpy(), wd), (n, k, off)
 
 
 @pytest.mark.parametrize("order", ["random", "far_first", "near_first", "all_equal"])
@@ -51,12 +51,11 @@ def test_nearest_k_sampled_bound(order, k):
         big = np.zeros((n + off, 2), dtype=np.float32)
         big[off:] = pts
         pt = torch.from_numpy(big).cuda()[off:]
-        idx = torch.empty(k, dtype=torch.int64, device="cuda")
-        d2 = torch.empty(k, dtype=torch.float32, device="cuda")
-        api.accr_nearest_k(pt, qx, qy, k, idx, d2, flags=api.ACCR_SYNC)
+        gi, gd = guarded((k,), torch.int64, -7), guarded((k,), torch.float32, -7)
+        api.accr_nearest_k(pt, qx, qy, k, gi.t, gd.t, flags=api.ACCR_SYNC)
         wi, wd = oracle.nearest_k(pts, qx, qy, k)
-        assert np.array_equal(idx.cpu().numpy(), wi), (order, k, off)
-        assert np.array_equal(d2.cpu().numpy(), wd), (order, k, off)
+        assert np.array_equal(gi.check("idx").cpu().numpy(), wi), (order, k, off)
+        assert np.array_equal(gd.check("d2").cpu().numpy(), wd), (order, k, off)
 
 
 def test_nearest_k_rejects_bad_k():
@@ -72,10 +71,11 @@ def test_nearest_k_rejects_bad_k():
 def test_standardize(n, form):
     x = (inputs.normal(n, np.float32, salt=n % 7) * 3 + 5).astype(np.float32)
     xt = torch.from_numpy(x).cuda()
-    y = torch.empty_like(xt)
-    st = torch.empty(2, dtype=torch.float64, device="cuda")
+    gy, gst = guarded((n,), torch.float32, float("nan")), guarded((2,), torch.float64, float("nan"))
+    y, st = gy.t, gst.t
     flags = {"fused": 0, "unfused": api.ACCR_UNFUSED, "host": api.ACCR_TWO_LEVEL_HOST}[form] | api.ACCR_SYNC
     api.accr_standardize(xt, y, st, flags=flags)
+    gy.check("y"), gst.check("stats")
     wy, (wm, wv) = oracle.standardize(x)
     mean, var = st.cpu().numpy()
     assert abs(mean - wm) <= 1e-9 * max(abs(wm), 1.0)
@@ -112,9 +112,9 @@ def test_grid_bfs_exact(mode, shape, p):
     grid, src = grid_case(*shape, p, seed=shape[0] * 31 + shape[1])
     want, wl = oracle.grid_bfs(grid, src)
     gt = torch.from_numpy(grid).cuda()
-    dist = torch.empty(shape, dtype=torch.int32, device="cuda")
-    levels = api.accr_grid_bfs(gt, src, dist, mode=mode)
-    assert np.array_equal(dist.cpu().numpy(), want)
+    dist = guarded(shape, torch.int32, 12345)
+    levels = api.accr_grid_bfs(gt, src, dist.t, mode=mode)
+    assert np.array_equal(dist.check("dist").cpu().numpy(), want)
     assert levels == wl
 
 
@@ -142,9 +142,9 @@ def test_grid_bfs_serpentine_many_levels():
     assert wl > 2000
     gt = torch.from_numpy(grid).cuda()
     for mode in ["persistent", "persistent", "guarded", "persistent"]:
-        dist = torch.empty((rows, cols), dtype=torch.int32, device="cuda")
-        assert api.accr_grid_bfs(gt, src, dist, mode=mode) == wl
-        assert np.array_equal(dist.cpu().numpy(), want)
+        dist = guarded((rows, cols), torch.int32, 12345)
+        assert api.accr_grid_bfs(gt, src, dist.t, mode=mode) == wl
+        assert np.array_equal(dist.check("dist").cpu().numpy(), want)
 
 
 @pytest.mark.slow
@@ -153,9 +153,8 @@ def test_nearest_k_full_size():
     n = 1 << 26
     pts = (inputs.rng(21, 5).random((n, 2), dtype=np.float32) * 100).astype(np.float32)
     pt = torch.from_numpy(pts).cuda()
-    idx = torch.empty(5, dtype=torch.int64, device="cuda")
-    d2 = torch.empty(5, dtype=torch.float32, device="cuda")
-    api.accr_nearest_k(pt, 41.5, 58.25, 5, idx, d2, flags=api.ACCR_SYNC)
+    gi, gd = guarded((5,), torch.int64, -7), guarded((5,), torch.float32, -7)
+    api.accr_nearest_k(pt, 41.5, 58.25, 5, gi.t, gd.t, flags=api.ACCR_SYNC)
     wi, wd = oracle.nearest_k(pts, 41.5, 58.25, 5)
-    assert np.array_equal(idx.cpu().numpy(), wi)
-    assert np.array_equal(d2.cpu().numpy(), wd)
+    assert np.array_equal(gi.check("idx").cpu().numpy(), wi)
+    assert np.array_equal(gd.check("d2").cpu().numpy(), wd)

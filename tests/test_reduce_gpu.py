@@ -4,6 +4,7 @@ import pytest
 import torch
 
 import oracle
+from guard import guarded
 from paper_1412_1127_gb300 import api, inputs
 from tolerances import (TOL_F32, TOL_F32_COMP, TOL_F64, assert_sum_close, same_bits)
 
@@ -26,9 +27,9 @@ def to_dev(x, offset=0):
 
 def gpu_reduce(x, op, acc, init=None, flags=0, offset=0):
     xt = to_dev(x, offset)
-    out = torch.full((1,), 7, dtype=TD[acc], device="cuda")
-    api.accr_reduce(xt, [api.clause(op, out, init)], flags=flags)
-    return out.cpu().numpy()[0]
+    out = guarded((1,), TD[acc], 7)
+    api.accr_reduce(xt, [api.clause(op, out.t, init)], flags=flags)
+    return out.check("%s into %s" % (op, acc)).cpu().numpy()[0]
 
 
 def int_input(op, n, t, salt):

@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+from guard import guarded
 from paper_1412_1127_gb300 import api, inputs
 from tolerances import TOL_F32, TOL_F32_COMP, same_bits
 
@@ -20,9 +21,9 @@ def gpu_rows(A_np, op, acc, init=None, flags=0, pad=0, offset=0):
     big = np.zeros((rows, cols + pad + offset), dtype=A_np.dtype)
     big[:, offset:offset + cols] = A_np
     t = torch.from_numpy(big).cuda()[:, offset:offset + cols]
-    out = torch.full((rows,), 9, dtype=TD[acc], device="cuda")
-    api.accr_rowreduce(t, [api.clause(op, out, init)], flags=flags)
-    return out.cpu().numpy()
+    out = guarded((rows,), TD[acc], 9)
+    api.accr_rowreduce(t, [api.clause(op, out.t, init)], flags=flags)
+    return out.check("row %s into %s, %dx%d" % (op, acc, rows, cols)).cpu().numpy()
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -63,10 +64,9 @@ def test_two_clauses_rows_full_size():
     # row sum and row max of a 65536 x 4096 U(-1,1) float matrix in one pass
     A = inputs.uniform_matrix(65536, 4096)
     At = torch.from_numpy(A).cuda()
-    s = torch.empty(65536, dtype=torch.float32, device="cuda")
-    m = torch.empty(65536, dtype=torch.float32, device="cuda")
-    api.accr_rowreduce(At, [api.clause("add", s), api.clause("max", m)])
-    m_np, s_np = m.cpu().numpy(), s.cpu().numpy()
+    gs, gm = guarded((65536,), torch.float32), guarded((65536,), torch.float32)
+    api.accr_rowreduce(At, [api.clause("add", gs.t), api.clause("max", gm.t)])
+    m_np, s_np = gm.check("row max").cpu().numpy(), gs.check("row sum").cpu().numpy()
     assert same_bits(m_np, oracle.rowreduce(A, "max"))
     idx = np.random.default_rng(0).choice(65536, size=64, replace=False)
     for r in idx:
@@ -95,11 +95,10 @@ def test_sum_and_extreme_pairs(t, acc, flags, ext, sum_first, shape):
         A = A.astype(np.float64) if t == "f64" else A
     At = torch.from_numpy(A).cuda()
     rows, cols = shape
-    s = torch.full((rows,), 9, dtype=TD[acc], device="cuda")
-    m = torch.full((rows,), 9, dtype=TD[t], device="cuda")
-    cls = [api.clause("add", s), api.clause(ext, m)]
+    gs, gm = guarded((rows,), TD[acc], 9), guarded((rows,), TD[t], 9)
+    cls = [api.clause("add", gs.t), api.clause(ext, gm.t)]
     api.accr_rowreduce(At, cls if sum_first else cls[::-1], flags=flags)
-    s_np, m_np = s.cpu().numpy(), m.cpu().numpy()
+    s_np, m_np = gs.check("row sum").cpu().numpy(), gm.check("row " + ext).cpu().numpy()
     want_m = oracle.rowreduce(A, ext, t) if t in ("i32", "i64") else oracle.rowreduce(A, ext)
     if t in ("i32", "i64"):
         assert np.array_equal(m_np, want_m)
@@ -117,8 +116,7 @@ def test_generic_two_clause_rows():
     g = np.random.default_rng(5)
     A = g.integers(-(1 << 31), 1 << 31, size=(77, 3000), dtype=np.int64).astype(np.int32)
     At = torch.from_numpy(A).cuda()
-    p = torch.empty(77, dtype=torch.int64, device="cuda")
-    x = torch.empty(77, dtype=torch.int32, device="cuda")
-    api.accr_rowreduce(At, [api.clause("mul", p), api.clause("bxor", x)])
-    assert np.array_equal(p.cpu().numpy(), oracle.rowreduce(A, "mul", "i64"))
-    assert np.array_equal(x.cpu().numpy(), oracle.rowreduce(A, "bxor", "i32"))
+    p, x = guarded((77,), torch.int64), guarded((77,), torch.int32)
+    api.accr_rowreduce(At, [api.clause("mul", p.t), api.clause("bxor", x.t)])
+    assert np.array_equal(p.check("row product").cpu().numpy(), oracle.rowreduce(A, "mul", "i64"))
+    assert np.array_equal(x.check("row xor").cpu().numpy(), oracle.rowreduce(A, "bxor", "i32"))

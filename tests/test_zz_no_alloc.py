@@ -4,9 +4,11 @@ arena, loops that cannot take the synchronisation cudaMalloc/cudaFree cause).
 Its block partials live in a fixed array inside the library instead of
 library-allocated scratch.
 
-Checked through the C ABI against accr_reduce on the same inputs, two calls in
-a row (the array keeps the previous call's contents, so the second call shows
-that nothing stale leaks in).  The file name sorts last so that a run that
+Checked through the C ABI against accr_reduce on the same inputs, over
+calls in a row that alternate between two inputs of different lengths (so the
+grid, the number of partials and their values differ from one call to the
+next): the array keeps the previous call's contents, and a call that read any
+of them, or found a counter left over, would give a different result.  The file name sorts last so that a run that
 stops at the first failure has already run every other test; it also passes
 alone in a fresh process."""
 import numpy as np
@@ -53,19 +55,21 @@ def run(fn, xt, clauses, flags):
 @pytest.mark.parametrize("t,clauses,flags", CASES)
 @pytest.mark.parametrize("n", [0, 5, (1 << 22) + 3])
 def test_noalloc_matches_reduce(t, clauses, flags, n):
-    x = make(t, n, salt=n % 13)
-    xt = torch.from_numpy(x).cuda()
-    want = run(api.accr_reduce, xt, clauses, flags)
-    for call in range(2):  # two calls in a row share the fixed array
+    other = 70001 if n != 70001 else 5          # a second input, another grid
+    xs = [make(t, n, salt=n % 13), make(t, other, salt=7)]
+    xts = [torch.from_numpy(x).cuda() for x in xs]
+    wants = [run(api.accr_reduce, xt, clauses, flags) for xt in xts]
+    for call in range(4):  # calls in a row share the fixed array, alternating inputs
+        x, xt, want = xs[call % 2], xts[call % 2], wants[call % 2]
         got = run(api.accr_reduce_noalloc, xt, clauses, flags)
         for (op, acc), g, w in zip(clauses, got, want):
-            if acc in ("i32", "i64") or op in ("max", "min") or n == 0:
+            if acc in ("i32", "i64") or op in ("max", "min") or x.size == 0:
                 assert g == w, (call, op, acc, g, w)
             else:
                 tol = TOL[(t if acc == t else "f64", 1 if flags else 0)]
                 assert_sum_close(g, x, tol)
-                assert abs(g - w) <= tol * max(abs(w), 0.1 * max(n, 1) ** 0.5)
-        if n > 0 and t == "i32":
+                assert abs(g - w) <= tol * max(abs(w), 0.1 * max(x.size, 1) ** 0.5)
+        if x.size > 0 and t == "i32":
             assert got[0] == int(oracle.reduce(x, clauses[0][0], clauses[0][1]))
 
 
@@ -73,16 +77,24 @@ def test_noalloc_allocates_nothing_and_rejects_host_form():
     x = inputs.full_range_i32((1 << 20) + 1)
     xt = torch.from_numpy(x).cuda()
     s = torch.empty(1, dtype=torch.int64, device="cuda")
+    y = inputs.full_range_i32(3001, salt=4)
+    yt = torch.from_numpy(y).cuda()
+    s2 = torch.empty(1, dtype=torch.int64, device="cuda")
     fresh = torch.cuda.Stream()
     api.accr_reduce_noalloc(xt, [api.clause("add", s)], stream=fresh)   # first call: set-up
     torch.cuda.synchronize()
+    s.fill_(-12345)                     # the measured calls must write the results
+    s2.fill_(-12345)
+    torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
-    for _ in range(2):
-        api.accr_reduce_noalloc(xt, [api.clause("add", s)], stream=torch.cuda.Stream())
+    st = torch.cuda.Stream()            # one stream: the calls must not overlap
+    api.accr_reduce_noalloc(xt, [api.clause("add", s)], stream=st)
+    api.accr_reduce_noalloc(yt, [api.clause("add", s2)], stream=st)
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
     assert int(s.item()) == int(oracle.reduce(x, "add", "i64"))
+    assert int(s2.item()) == int(oracle.reduce(y, "add", "i64"))
     arr, keep = api._clauses([api.clause("add", s)])
     rc = api.lib().accr_reduce_noalloc(xt.data_ptr(), xt.numel(), api.ACCR_I32, arr, 1,
                                        api.ACCR_TWO_LEVEL_HOST, None)
