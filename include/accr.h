@@ -367,8 +367,10 @@ ACCR_API int accr_server_create(uint64_t hbm_budget_bytes, int32_t nstreams,
 
 /* Queue one region (`clauses[c].out` is ignored: results come back through
  * accr_poll).  Returns ACCR_EBUDGET if the region alone exceeds the budget.
- * The descriptor is copied; the region's elements must stay valid until its
- * result has been polled. */
+ * The descriptor is copied, and so is each clause's prior value (`init`): the
+ * caller may reuse or free the descriptor and the prior values as soon as
+ * this returns.  The region's elements must stay valid until its result has
+ * been polled. */
 ACCR_API int accr_submit(accr_server *server, const accr_region *region,
                          uint64_t *ticket);
 
@@ -413,7 +415,9 @@ ACCR_API int accr_server_replay(accr_server *server, const accr_region *regions,
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call clears the counter on `stream` before
+ * before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys the device's
+ * primary context) calls on that device are not valid.  Every call clears the counter on `stream` before
  * its launch.  All calls share the one array: calls that overlap on the GPU
  * (different streams or threads) race on it and give wrong results, so
  * serialise them.  Allocates nothing: no cudaMalloc, cudaFree or allocating

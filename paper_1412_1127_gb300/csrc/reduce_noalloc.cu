@@ -12,7 +12,8 @@
 // bytes.  Every GPU that loads the library holds it until the process exits.
 // In host code its name only stands in for the device variable, so the
 // device address is looked up once per device with cudaGetSymbolAddress (on
-// the first call made with that device current) and cached.
+// the first call made with that device current) and cached for the life of
+// the process, so calls after cudaDeviceReset on that device are not valid.
 //
 // All calls share the array: calls that overlap on the GPU (on different
 // streams, or from different threads) race on it and give wrong results.  The

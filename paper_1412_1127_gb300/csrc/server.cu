@@ -39,7 +39,9 @@ static int64_t now_ns() {
 
 struct Req {
     uint64_t ticket;
-    accr_region region;
+    accr_region region;  // its clauses' init pointers point at nothing the caller owns (see init)
+    uint64_t init[ACCR_MAX_CLAUSES];  // each clause's prior value, copied at submit
+    uint32_t has_init;                // bit c: clause c had a prior value
     int64_t bytes;
     int64_t submit_ns;
 };
@@ -146,8 +148,12 @@ int accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
     for (size_t i = 0; i < s.reqs.size(); ++i) {
         regs[i] = s.reqs[i].region;
         // the kernel stores each variable straight into the pinned result slots
-        // (no device-to-host copy in the batch's critical path)
-        for (int c = 0; c < regs[i].nclauses; ++c) regs[i].clauses[c].out = &s.host_res[i * ACCR_MAX_CLAUSES + c];
+        // (no device-to-host copy in the batch's critical path); prior values
+        // come from the request's own copy
+        for (int c = 0; c < regs[i].nclauses; ++c) {
+            regs[i].clauses[c].out = &s.host_res[i * ACCR_MAX_CLAUSES + c];
+            regs[i].clauses[c].init = (s.reqs[i].has_init >> c & 1) ? (const void *)&s.reqs[i].init[c] : nullptr;
+        }
     }
     s.launch_ns = now_ns();
     int rc = batch_launch_regions(regs.data(), (int64_t)regs.size(), (accr_stream_t)s.stream, ACCR_SERVED_TILE_BYTES);
@@ -234,6 +240,17 @@ extern "C" ACCR_API int accr_submit(accr_server *S, const accr_region *region, u
     if (rc != ACCR_OK) return rc;
     Req q;
     q.region = *region;
+    // The caller may reuse or free its prior values as soon as this returns:
+    // keep a copy of each, read by the scheduler thread when the batch forms.
+    q.has_init = 0;
+    for (int c = 0; c < ACCR_MAX_CLAUSES; ++c) {
+        q.init[c] = 0;
+        if (c < region->nclauses && region->clauses[c].init) {
+            memcpy(&q.init[c], region->clauses[c].init, (size_t)type_bytes(region->clauses[c].acc_type));
+            q.has_init |= 1u << c;
+        }
+        q.region.clauses[c].init = nullptr;
+    }
     q.bytes = region->n * (int64_t)type_bytes(region->in_type);
     if (fault_take(ACCR_FAULT_ADMIT)) return set_error(ACCR_EBUDGET, "accr_submit: injected admission rejection");
     if ((uint64_t)q.bytes > S->budget)
