@@ -732,25 +732,32 @@ def measure_matmul(dev, length=4096, reps=5):
 
 def measure_fp32_peak(dev, rounds=1 << 15, reps=5):
     """Measured FP32 FMA peak (the SIMT nest's roofline): 16 independent FMA
-    chains per thread, 4 CTAs of 256 threads per SM."""
+    chains per thread, 4 CTAs of 256 threads per SM, issued as scalar
+    instructions and as packed pairs; the peak is the larger rate."""
     import torch
     from paper_1412_1127_gb300 import api
     ctas = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
     sink = torch.empty(256 * ctas, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(3):
-        api.accr_probe_fma(ctas, rounds, sink, stream=stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        api.accr_probe_fma(ctas, rounds, sink, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    flop = 2.0 * 16 * 256 * ctas * rounds
-    return {"tflops": round(flop / (ms * 1e-3) / 1e12, 2), "ms": round(ms, 4),
-            "probe": "%d CTAs x 256 threads x %d rounds x 16 FMA" % (ctas, rounds)}
+
+    def rate(fn, fmas):
+        for _ in range(3):
+            fn(ctas, rounds, sink, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn(ctas, rounds, sink, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return 2.0 * fmas * 256 * ctas * rounds / (ms * 1e-3) / 1e12, ms
+
+    scalar, ms_s = rate(api.accr_probe_fma, 16)
+    packed, ms_p = rate(api.accr_probe_fma_packed, 32)
+    return {"tflops": round(max(scalar, packed), 2), "scalar_tflops": round(scalar, 2),
+            "packed_tflops": round(packed, 2), "ms": round(ms_s, 4), "ms_packed": round(ms_p, 4),
+            "probe": "%d CTAs x 256 threads x %d rounds x 16 chains (scalar FMA, or packed pairs)" % (ctas, rounds)}
 
 
 def measure_small_region(dev, n=1 << 20, reps=100):

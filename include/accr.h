@@ -458,6 +458,12 @@ ACCR_API int accr_selftest_wait_timeout(uint32_t tries, accr_stream_t stream);
  * or a NULL sink. */
 ACCR_API int accr_probe_fma(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream);
 
+/* The same probe issuing packed pairs (two float fused multiply-adds per
+ * instruction): 16 independent pair chains per thread, i.e.
+ * 2 * 32 * 256 * ctas * rounds flop.  Arguments, results and errors as for
+ * accr_probe_fma.  The FP32 peak is the larger of the two probes' rates. */
+ACCR_API int accr_probe_fma_packed(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream);
+
 /* Message of the last error raised on the calling thread ("" if none). */
 ACCR_API const char *accr_last_error(void);
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "accr_fault_inject": (ctypes.c_int, [_i32, _i64]),
     "accr_selftest_wait_timeout": (ctypes.c_int, [_u32, _vp]),
     "accr_probe_fma": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
+    "accr_probe_fma_packed": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
     "accr_last_error": (ctypes.c_char_p, []),
     "accr_launch_count": (_u64, []),
     "accr_version": (_i32, []),

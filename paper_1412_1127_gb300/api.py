@@ -322,6 +322,12 @@ def accr_probe_fma(ctas, rounds, sink, stream=None):
     return check(lib().accr_probe_fma(int(ctas), int(rounds), sink.data_ptr(), _stream(stream)))
 
 
+def accr_probe_fma_packed(ctas, rounds, sink, stream=None):
+    """FP32 peak probe with packed pairs (2 * 32 * 256 * ctas * rounds flop)."""
+    assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= 256 * ctas
+    return check(lib().accr_probe_fma_packed(int(ctas), int(rounds), sink.data_ptr(), _stream(stream)))
+
+
 def accr_selftest_wait_timeout(tries=1000, stream=None):
     """Runs the bounded-wait self-test; returns its status code (ACCR_ETIMEDOUT expected)."""
     return int(lib().accr_selftest_wait_timeout(int(tries), _stream(stream)))

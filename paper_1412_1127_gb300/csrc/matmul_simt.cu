@@ -27,16 +27,34 @@ constexpr int MT = 128;   // CTA tile (rows and columns of c)
 constexpr int KT = 16;    // k slice per stage
 constexpr int NTH = 256;  // threads per CTA
 
+// Two lanes of float arithmetic per instruction (sm_100 family packed f32x2):
+// each half is an ordinary round-to-nearest float operation, so the results
+// are those of the scalar instructions, bit for bit, at half the issue slots.
+// A packed pair travels as one 64-bit register.
+typedef unsigned long long f2;
+
 template <bool SERIAL>
-__device__ __forceinline__ float mac(float acc, float x, float y) {
-    if constexpr (SERIAL) return __fadd_rn(acc, __fmul_rn(x, y));
-    else return __fmaf_rn(x, y, acc);
+__device__ __forceinline__ f2 mac2(f2 acc, f2 x, f2 y) {
+    f2 d;
+    if constexpr (SERIAL) {
+        f2 p;
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(x), "l"(y));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(acc), "l"(p));
+    } else {
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(x), "l"(y), "l"(acc));
+    }
+    return d;
 }
+
+__device__ __forceinline__ float lo_of(f2 v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float hi_of(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
 
 template <bool SERIAL, bool VEC>
 __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__restrict__ a, const float *__restrict__ b,
                                                              float *__restrict__ c, int64_t len) {
-    __shared__ __align__(16) float As[2][KT][MT];  // a slice, transposed: As[k][row]
+    // a slice, transposed and with every value stored twice: As[k][row] = (a, a),
+    // so one 16-byte read gives two packed operands (a_r, a_r), (a_r+1, a_r+1)
+    __shared__ __align__(16) float2 As[2][KT][MT];
     __shared__ __align__(16) float Bs[2][KT][MT];  // b slice: Bs[k][col]
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -72,19 +90,21 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
     auto store_tiles = [&](int buf, const float4 (&va)[2], const float4 (&vb)[2]) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            As[buf][a_k + 0][a_r + h * 64] = va[h].x;
-            As[buf][a_k + 1][a_r + h * 64] = va[h].y;
-            As[buf][a_k + 2][a_r + h * 64] = va[h].z;
-            As[buf][a_k + 3][a_r + h * 64] = va[h].w;
+            As[buf][a_k + 0][a_r + h * 64] = make_float2(va[h].x, va[h].x);
+            As[buf][a_k + 1][a_r + h * 64] = make_float2(va[h].y, va[h].y);
+            As[buf][a_k + 2][a_r + h * 64] = make_float2(va[h].z, va[h].z);
+            As[buf][a_k + 3][a_r + h * 64] = make_float2(va[h].w, va[h].w);
             *reinterpret_cast<float4 *>(&Bs[buf][b_k + h * 8][b_c]) = vb[h];
         }
     };
 
-    float acc[8][8];
+    // acc[i][q]: row i of the thread's 8 x 8 block, columns 2q and 2q+1 of its
+    // column set {tx*4 .. tx*4+3, 64+tx*4 .. 64+tx*4+3}, as one packed pair
+    f2 acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[i][q] = 0ull;
 
     float4 va[2], vb[2];
 #pragma unroll
@@ -105,30 +125,21 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
                 load_b((kt + 1) * KT, h, vb[h]);
             }
         }
-        // operand fragments double-buffered in registers: k+1 is read from
-        // shared memory while the 64 products of k issue
-        float4 fa[2][2], fb[2][2];
-        fa[0][0] = *reinterpret_cast<const float4 *>(&As[cur][0][ty * 4]);
-        fa[0][1] = *reinterpret_cast<const float4 *>(&As[cur][0][64 + ty * 4]);
-        fb[0][0] = *reinterpret_cast<const float4 *>(&Bs[cur][0][tx * 4]);
-        fb[0][1] = *reinterpret_cast<const float4 *>(&Bs[cur][0][64 + tx * 4]);
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
-            const int p = k & 1;
-            if (k + 1 < KT) {
-                fa[p ^ 1][0] = *reinterpret_cast<const float4 *>(&As[cur][k + 1][ty * 4]);
-                fa[p ^ 1][1] = *reinterpret_cast<const float4 *>(&As[cur][k + 1][64 + ty * 4]);
-                fb[p ^ 1][0] = *reinterpret_cast<const float4 *>(&Bs[cur][k + 1][tx * 4]);
-                fb[p ^ 1][1] = *reinterpret_cast<const float4 *>(&Bs[cur][k + 1][64 + tx * 4]);
-            }
-            const float ar[8] = {fa[p][0].x, fa[p][0].y, fa[p][0].z, fa[p][0].w,
-                                 fa[p][1].x, fa[p][1].y, fa[p][1].z, fa[p][1].w};
-            const float br[8] = {fb[p][0].x, fb[p][0].y, fb[p][0].z, fb[p][0].w,
-                                 fb[p][1].x, fb[p][1].y, fb[p][1].z, fb[p][1].w};
+            // rows ty*4 .. +3 and 64+ty*4 .. +3 as duplicated pairs; columns as pairs
+            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][ty * 4]);
+            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][ty * 4 + 2]);
+            const ulonglong2 a45 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][64 + ty * 4]);
+            const ulonglong2 a67 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][64 + ty * 4 + 2]);
+            const ulonglong2 b03 = *reinterpret_cast<const ulonglong2 *>(&Bs[cur][k][tx * 4]);
+            const ulonglong2 b47 = *reinterpret_cast<const ulonglong2 *>(&Bs[cur][k][64 + tx * 4]);
+            const f2 ar[8] = {a01.x, a01.y, a23.x, a23.y, a45.x, a45.y, a67.x, a67.y};
+            const f2 br[4] = {b03.x, b03.y, b47.x, b47.y};
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = mac<SERIAL>(acc[i][j], ar[i], br[j]);
+                for (int q = 0; q < 4; ++q) acc[i][q] = mac2<SERIAL>(acc[i][q], ar[i], br[q]);
         }
         if (more) store_tiles(cur ^ 1, va, vb);
         __syncthreads();
@@ -141,7 +152,8 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t cc = col0 + h * 64 + tx * 4;
-            float4 v = make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
+            const f2 p0 = acc[i][2 * h], p1 = acc[i][2 * h + 1];
+            float4 v = make_float4(lo_of(p0), hi_of(p0), lo_of(p1), hi_of(p1));
             if (VEC && cc + 3 < len) {
                 *reinterpret_cast<float4 *>(c + r * len + cc) = v;
             } else {
@@ -173,6 +185,28 @@ __global__ void __launch_bounds__(PROBE_THREADS) fma_probe_kernel(int64_t rounds
     sink[(int64_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = s * (1.f / 16.f);
 }
 
+// The same probe issuing packed pairs: 16 independent f32x2 chains per thread,
+// 32 fused multiply-adds per round.  If the packed form moves more float work
+// per clock than scalar instructions, this is the FP32 peak.
+__global__ void __launch_bounds__(PROBE_THREADS) fma2_probe_kernel(int64_t rounds, float *sink, float b, float c) {
+    f2 a[16];
+    const f2 bb = ((f2)__float_as_uint(b) << 32) | __float_as_uint(b);
+    const f2 cc = ((f2)__float_as_uint(c) << 32) | __float_as_uint(c);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float lo = (float)(threadIdx.x + i) * 1e-3f, hi = (float)(threadIdx.x + i + 16) * 1e-3f;
+        a[i] = ((f2)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+    }
+    for (int64_t r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[i]) : "l"(bb), "l"(cc));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += lo_of(a[i]) + hi_of(a[i]);
+    sink[(int64_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = s * (1.f / 32.f);
+}
+
 int matmul_simt(const float *a, const float *b, float *c, int64_t len, bool serial, cudaStream_t s) {
     if (len == 0) return ACCR_OK;
     const int64_t tiles = (len + MT - 1) / MT;
@@ -201,4 +235,13 @@ extern "C" ACCR_API int accr_probe_fma(int32_t ctas, int64_t rounds, float *sink
     if (rc != ACCR_OK) return rc;
     accr::fma_probe_kernel<<<ctas, accr::PROBE_THREADS, 0, (cudaStream_t)stream>>>(rounds, sink, 0.999f, 0.001f);
     return accr::launched("fma_probe_kernel");
+}
+
+extern "C" ACCR_API int accr_probe_fma_packed(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream) {
+    accr::clear_error();
+    if (ctas < 1 || rounds < 1 || !sink) return accr::set_error(ACCR_EINVAL, "accr_probe_fma_packed: bad arguments");
+    int rc = accr::launch_guard("fma2_probe_kernel");
+    if (rc != ACCR_OK) return rc;
+    accr::fma2_probe_kernel<<<ctas, accr::PROBE_THREADS, 0, (cudaStream_t)stream>>>(rounds, sink, 0.999f, 0.001f);
+    return accr::launched("fma2_probe_kernel");
 }

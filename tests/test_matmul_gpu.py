@@ -143,3 +143,9 @@ def test_fma_probe():
     assert np.all(np.abs(s - 1.0) < 1e-3), (s.min(), s.max())
     with pytest.raises(api._native.AccrError):
         api.accr_probe_fma(0, 10, sink)
+    sink.zero_()
+    api.accr_probe_fma_packed(8, 20000, sink)
+    s = sink.cpu().numpy()
+    assert np.all(np.abs(s - 1.0) < 1e-3), (s.min(), s.max())
+    with pytest.raises(api._native.AccrError):
+        api.accr_probe_fma_packed(8, 0, sink)
