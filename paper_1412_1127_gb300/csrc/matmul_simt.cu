@@ -27,34 +27,16 @@ constexpr int MT = 128;   // CTA tile (rows and columns of c)
 constexpr int KT = 16;    // k slice per stage
 constexpr int NTH = 256;  // threads per CTA
 
-// Two lanes of float arithmetic per instruction (sm_100 family packed f32x2):
-// each half is an ordinary round-to-nearest float operation, so the results
-// are those of the scalar instructions, bit for bit, at half the issue slots.
-// A packed pair travels as one 64-bit register.
-typedef unsigned long long f2;
-
 template <bool SERIAL>
-__device__ __forceinline__ f2 mac2(f2 acc, f2 x, f2 y) {
-    f2 d;
-    if constexpr (SERIAL) {
-        f2 p;
-        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(x), "l"(y));
-        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(acc), "l"(p));
-    } else {
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(x), "l"(y), "l"(acc));
-    }
-    return d;
+__device__ __forceinline__ float mac(float acc, float x, float y) {
+    if constexpr (SERIAL) return __fadd_rn(acc, __fmul_rn(x, y));
+    else return __fmaf_rn(x, y, acc);
 }
-
-__device__ __forceinline__ float lo_of(f2 v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
-__device__ __forceinline__ float hi_of(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
 
 template <bool SERIAL, bool VEC>
 __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__restrict__ a, const float *__restrict__ b,
                                                              float *__restrict__ c, int64_t len) {
-    // a slice, transposed and with every value stored twice: As[k][row] = (a, a),
-    // so one 16-byte read gives two packed operands (a_r, a_r), (a_r+1, a_r+1)
-    __shared__ __align__(16) float2 As[2][KT][MT];
+    __shared__ __align__(16) float As[2][KT][MT];  // a slice, transposed: As[k][row]
     __shared__ __align__(16) float Bs[2][KT][MT];  // b slice: Bs[k][col]
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -90,21 +72,19 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
     auto store_tiles = [&](int buf, const float4 (&va)[2], const float4 (&vb)[2]) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            As[buf][a_k + 0][a_r + h * 64] = make_float2(va[h].x, va[h].x);
-            As[buf][a_k + 1][a_r + h * 64] = make_float2(va[h].y, va[h].y);
-            As[buf][a_k + 2][a_r + h * 64] = make_float2(va[h].z, va[h].z);
-            As[buf][a_k + 3][a_r + h * 64] = make_float2(va[h].w, va[h].w);
+            As[buf][a_k + 0][a_r + h * 64] = va[h].x;
+            As[buf][a_k + 1][a_r + h * 64] = va[h].y;
+            As[buf][a_k + 2][a_r + h * 64] = va[h].z;
+            As[buf][a_k + 3][a_r + h * 64] = va[h].w;
             *reinterpret_cast<float4 *>(&Bs[buf][b_k + h * 8][b_c]) = vb[h];
         }
     };
 
-    // acc[i][q]: row i of the thread's 8 x 8 block, columns 2q and 2q+1 of its
-    // column set {tx*4 .. tx*4+3, 64+tx*4 .. 64+tx*4+3}, as one packed pair
-    f2 acc[8][4];
+    float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = 0ull;
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
     float4 va[2], vb[2];
 #pragma unroll
@@ -125,21 +105,30 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
                 load_b((kt + 1) * KT, h, vb[h]);
             }
         }
+        // operand fragments double-buffered in registers: k+1 is read from
+        // shared memory while the 64 products of k issue
+        float4 fa[2][2], fb[2][2];
+        fa[0][0] = *reinterpret_cast<const float4 *>(&As[cur][0][ty * 4]);
+        fa[0][1] = *reinterpret_cast<const float4 *>(&As[cur][0][64 + ty * 4]);
+        fb[0][0] = *reinterpret_cast<const float4 *>(&Bs[cur][0][tx * 4]);
+        fb[0][1] = *reinterpret_cast<const float4 *>(&Bs[cur][0][64 + tx * 4]);
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
-            // rows ty*4 .. +3 and 64+ty*4 .. +3 as duplicated pairs; columns as pairs
-            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][ty * 4]);
-            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][ty * 4 + 2]);
-            const ulonglong2 a45 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][64 + ty * 4]);
-            const ulonglong2 a67 = *reinterpret_cast<const ulonglong2 *>(&As[cur][k][64 + ty * 4 + 2]);
-            const ulonglong2 b03 = *reinterpret_cast<const ulonglong2 *>(&Bs[cur][k][tx * 4]);
-            const ulonglong2 b47 = *reinterpret_cast<const ulonglong2 *>(&Bs[cur][k][64 + tx * 4]);
-            const f2 ar[8] = {a01.x, a01.y, a23.x, a23.y, a45.x, a45.y, a67.x, a67.y};
-            const f2 br[4] = {b03.x, b03.y, b47.x, b47.y};
+            const int p = k & 1;
+            if (k + 1 < KT) {
+                fa[p ^ 1][0] = *reinterpret_cast<const float4 *>(&As[cur][k + 1][ty * 4]);
+                fa[p ^ 1][1] = *reinterpret_cast<const float4 *>(&As[cur][k + 1][64 + ty * 4]);
+                fb[p ^ 1][0] = *reinterpret_cast<const float4 *>(&Bs[cur][k + 1][tx * 4]);
+                fb[p ^ 1][1] = *reinterpret_cast<const float4 *>(&Bs[cur][k + 1][64 + tx * 4]);
+            }
+            const float ar[8] = {fa[p][0].x, fa[p][0].y, fa[p][0].z, fa[p][0].w,
+                                 fa[p][1].x, fa[p][1].y, fa[p][1].z, fa[p][1].w};
+            const float br[8] = {fb[p][0].x, fb[p][0].y, fb[p][0].z, fb[p][0].w,
+                                 fb[p][1].x, fb[p][1].y, fb[p][1].z, fb[p][1].w};
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[i][q] = mac2<SERIAL>(acc[i][q], ar[i], br[q]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = mac<SERIAL>(acc[i][j], ar[i], br[j]);
         }
         if (more) store_tiles(cur ^ 1, va, vb);
         __syncthreads();
@@ -152,8 +141,7 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t cc = col0 + h * 64 + tx * 4;
-            const f2 p0 = acc[i][2 * h], p1 = acc[i][2 * h + 1];
-            float4 v = make_float4(lo_of(p0), hi_of(p0), lo_of(p1), hi_of(p1));
+            float4 v = make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
             if (VEC && cc + 3 < len) {
                 *reinterpret_cast<float4 *>(c + r * len + cc) = v;
             } else {
@@ -164,6 +152,19 @@ __global__ void __launch_bounds__(NTH, 2) matmul_simt_kernel(const float *__rest
             }
         }
     }
+}
+
+
+// Packed pairs of floats (sm_100 family f32x2): each half is an ordinary
+// round-to-nearest fused multiply-add.  Used only by the packed FP32 probe:
+// measured on GB300, a packed instruction moves no more float work per clock
+// than two scalar ones (the FMA pipe is the limit either way).
+typedef unsigned long long f2;
+
+__device__ __forceinline__ float lo_of(f2 v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float hi_of(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2 pack2(float lo, float hi) {
+    return ((f2)__float_as_uint(hi) << 32) | (f2)__float_as_uint(lo);
 }
 
 // FP32 peak probe: 16 independent FMA chains per thread (latency hidden by
@@ -190,12 +191,11 @@ __global__ void __launch_bounds__(PROBE_THREADS) fma_probe_kernel(int64_t rounds
 // per clock than scalar instructions, this is the FP32 peak.
 __global__ void __launch_bounds__(PROBE_THREADS) fma2_probe_kernel(int64_t rounds, float *sink, float b, float c) {
     f2 a[16];
-    const f2 bb = ((f2)__float_as_uint(b) << 32) | __float_as_uint(b);
-    const f2 cc = ((f2)__float_as_uint(c) << 32) | __float_as_uint(c);
+    const f2 bb = pack2(b, b), cc = pack2(c, c);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const float lo = (float)(threadIdx.x + i) * 1e-3f, hi = (float)(threadIdx.x + i + 16) * 1e-3f;
-        a[i] = ((f2)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+        a[i] = pack2(lo, hi);
     }
     for (int64_t r = 0; r < rounds; ++r) {
 #pragma unroll
