@@ -416,7 +416,7 @@ def run_scalar(args):
         torch.cuda.empty_cache()
         extra["matmul"] = measure_matmul(dev)
         torch.cuda.empty_cache()
-        extra["rows"] = measure_rows(dev)
+        extra["rows"] = measure_rows_all(dev)
         torch.cuda.empty_cache()
         extra["patterns"] = measure_patterns(dev)
         torch.cuda.empty_cache()
@@ -834,16 +834,29 @@ def measure_rows(dev, rows=65536, cols=4096, steps=10, warmup=3):
     nbytes = rows * cols * 4
     peaks, kind = measured_peaks()
     ok_max = bool(torch.equal(m, At.amax(dim=1)))
-    return {"workload": "row sum + row max (one pass), %d x %d float U(-1,1)" % (rows, cols),
+    form = "split-row (each row cut into CTA tiles)" if cols * 4 >= (256 << 10) else "one warp per row"
+    return {"workload": "row sum + row max (one pass), %d x %d float U(-1,1)" % (rows, cols), "form": form,
             "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
             "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]), 4),
             "row_max_equals_torch_amax": ok_max}
 
 
+def measure_rows_all(dev, rows=65536, steps=10, warmup=3):
+    """The 65536 x 4096 row nest, plus a few long rows (4 x 2^24 and
+    64 x 2^22, the split-row form) under the same name."""
+    import torch
+    out = measure_rows(dev, rows, 4096, steps, warmup)
+    out["long_rows"] = []
+    for r, c in [(4, 1 << 24), (64, 1 << 22)]:
+        out["long_rows"].append(measure_rows(dev, r, c, steps, warmup))
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_rows(args):
     import torch
     torch.cuda.set_device(0)
-    print(json.dumps(measure_rows(torch.device("cuda", 0), args.rows_m, 4096, args.steps, args.warmup)), flush=True)
+    print(json.dumps(measure_rows_all(torch.device("cuda", 0), args.rows_m, args.steps, args.warmup)), flush=True)
     return 0
 
 

@@ -2,20 +2,41 @@
 // one reduction variable per row of a row-major matrix (the two-level loop
 // shape of Listing 1a with an inner reduction; IPMACC Sec. 1.3, Stage 3.4).
 //
-// Mapping: gang -> CTA, worker -> warp, vector -> lane.  One warp owns a row,
-// so no cross-warp or cross-gang merge is needed: lanes stream the row in
-// 16-byte vectors (RU2 in flight per lane), merge through shuffles, and lane 0
-// writes the row's variable.  Rows whose start is not 16-byte aligned (ld not
-// a multiple of the vector) fold their head and tail element by element.
+// Mapping: gang -> CTA, worker -> warp, vector -> lane.  Two forms, chosen by
+// the row's length alone (so a row's result never depends on how many rows
+// the matrix has):
+//
+//   * rows shorter than SPLIT_ROW_BYTES: one warp owns a row, so no
+//     cross-warp or cross-gang merge is needed: lanes stream the row in
+//     16-byte vectors (RU2 in flight per lane), merge through shuffles, and
+//     lane 0 writes the row's variable.  Rows whose start is not 16-byte
+//     aligned (ld not a multiple of the vector) fold their head and tail
+//     element by element.
+//   * longer rows: each row is a region of one batched launch (batch.cu),
+//     cut into CTA tiles of split_tile_bytes(row bytes) (at least 256 tiles a
+//     row up to 2 MiB tiles); a tile's partial goes to scratch and the row's
+//     last tile merges the partials in tile order.  A few long rows then
+//     spread over every SM instead of over a few warps.
 #include <string.h>
 
 #include <mutex>
 #include <type_traits>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "fold.cuh"
 
 namespace accr {
+
+constexpr int64_t SPLIT_ROW_BYTES = 256 * 1024;
+
+// Tile of the split-row form: row bytes / 256 rounded down to a power of two,
+// within [64 KiB, 2 MiB].
+static int64_t split_tile_bytes(int64_t row_bytes) {
+    int64_t t = 64 * 1024;
+    while (t * 2 <= row_bytes / 256 && t < 2 * 1024 * 1024) t *= 2;
+    return t;
+}
 
 constexpr int WB = 256;  // threads per CTA (8 warps = 8 rows in flight)
 constexpr int RU2 = 8;   // 16-byte vectors per lane per iteration
@@ -190,6 +211,14 @@ extern "C" ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols
     if (cols > 0 && !A) return set_error(ACCR_EINVAL, "accr_rowreduce: A is NULL");
     if (((uintptr_t)A % (uintptr_t)type_bytes(in_type)) != 0)
         return set_error(ACCR_EINVAL, "accr_rowreduce: A is not aligned to its element size");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t row_bytes = cols * (int64_t)type_bytes(in_type);
+    if (row_bytes >= SPLIT_ROW_BYTES) {
+        rc = batch_launch_rows(A, rows, cols, ld, in_type, cl, nclauses, split_tile_bytes(row_bytes), stream);
+        if (rc != ACCR_OK) return rc;
+        if (flags & ACCR_SYNC) return cuda_check(cudaStreamSynchronize(s), "accr_rowreduce: sync");
+        return ACCR_OK;
+    }
     RowArgs a;
     memset(&a, 0, sizeof a);
     a.A = A;
@@ -198,7 +227,6 @@ extern "C" ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols
     a.ld = ld;
     a.nc = nclauses;
     for (int c = 0; c < nclauses; ++c) a.cl[c] = cl[c];
-    cudaStream_t s = (cudaStream_t)stream;
     switch (in_type) {
     case ACCR_I32: rc = row_launch<int32_t>(a, s); break;
     case ACCR_I64: rc = row_launch<int64_t>(a, s); break;

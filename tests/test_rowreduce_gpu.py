@@ -120,3 +120,46 @@ def test_generic_two_clause_rows():
     api.accr_rowreduce(At, [api.clause("mul", p.t), api.clause("bxor", x.t)])
     assert np.array_equal(p.check("row product").cpu().numpy(), oracle.rowreduce(A, "mul", "i64"))
     assert np.array_equal(x.check("row xor").cpu().numpy(), oracle.rowreduce(A, "bxor", "i32"))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape", [(4, 1 << 24), (64, 1 << 22)])
+def test_long_rows_split_path(shape):
+    """A few long rows (the split-row form: each row cut into CTA tiles):
+    every row's max bit-exact, every row's sum within the float tolerance of
+    its exact sum, the same bits on a repeat, and one row alone gives the
+    same bits as inside the matrix (the split depends on the row length only)."""
+    import concurrent.futures as cf
+    rows, cols = shape
+    A = inputs.uniform_matrix(rows, cols, salt=rows)
+    At = torch.from_numpy(A).cuda()
+    gs, gm = guarded((rows,), torch.float32), guarded((rows,), torch.float32)
+    api.accr_rowreduce(At, [api.clause("add", gs.t), api.clause("max", gm.t)])
+    s_np, m_np = gs.check("row sum").cpu().numpy(), gm.check("row max").cpu().numpy()
+    assert same_bits(m_np, oracle.rowreduce(A, "max"))
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        truths = list(ex.map(lambda r: oracle.truth_sum(A[r]), range(rows)))
+    for r, truth in enumerate(truths):
+        assert abs(float(s_np[r]) - truth) / max(abs(truth), 0.1 * math.sqrt(cols) * 0.577) <= TOL_F32, r
+    s2 = torch.empty(rows, dtype=torch.float32, device="cuda")
+    api.accr_rowreduce(At, [api.clause("add", s2)])
+    assert same_bits(s2.cpu().numpy(), s_np)
+    one = torch.empty(1, dtype=torch.float32, device="cuda")
+    api.accr_rowreduce(At[rows - 1:rows], [api.clause("add", one)])
+    assert same_bits(one.cpu().numpy(), s_np[rows - 1:rows])
+
+
+def test_long_integer_rows_split_path():
+    """Integer rows past the split-row threshold, with padded rows (ld not a
+    multiple of the vector) and three clauses (two passes over each row)."""
+    g = np.random.default_rng(17)
+    A = g.integers(-(1 << 40), 1 << 40, size=(3, (1 << 20) + 7), dtype=np.int64)
+    for pad, off in [(0, 0), (3, 1)]:
+        big = np.zeros((3, A.shape[1] + pad + off), dtype=np.int64)
+        big[:, off:off + A.shape[1]] = A
+        t = torch.from_numpy(big).cuda()[:, off:off + A.shape[1]]
+        outs = [guarded((3,), torch.int64, 5) for _ in range(3)]
+        api.accr_rowreduce(t, [api.clause("add", outs[0].t), api.clause("bxor", outs[1].t, init=9),
+                               api.clause("min", outs[2].t)])
+        for o, (op, init) in zip(outs, [("add", None), ("bxor", 9), ("min", None)]):
+            assert np.array_equal(o.check(op).cpu().numpy(), oracle.rowreduce(A, op, "i64", init=init)), (op, pad)
