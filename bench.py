@@ -623,18 +623,61 @@ def measure_served(dev, seconds=2.0, rate=50000.0):
     api.accr_server_replay(None, regions[:warm], arrivals[:warm], plain=True)
     resp = api.accr_server_replay(None, regions, arrivals, plain=True)
     st_s, st_p = latency_stats(res, count), latency_stats(resp, count)
-    # results: served and plain agree bit for bit on the integer regions
+    # results: served and plain agree bit for bit on the integer regions, and
+    # the float sums (compensated, each within 1e-5 of the exact sum) within
+    # twice that of each other
     same = all(list(res[i].value[:res[i].nclauses]) == list(resp[i].value[:resp[i].nclauses])
                for i in range(count) if meta[i][0] != "f32")
+    fdiff = 0.0
+    for i in range(count):
+        if meta[i][0] == "f32":
+            a = float(api.decode(res[i].value[0], torch.float32))
+            b = float(api.decode(resp[i].value[0], torch.float32))
+            fdiff = max(fdiff, abs(a - b) / max(abs(b), 0.1 * meta[i][2] ** 0.5))
+    out = {"workload": "served regions: Poisson arrivals at %d/s for %.1f s (%d regions, %.1f GB), lengths "
+                       "log-uniform [2^8, 2^26], float32 (+comp) / int32 (+, max) / int64 (+, ^), "
+                       "resident pools, 64 GiB budget, 4 stream slots" % (rate, seconds, count, nbytes / 1e9),
+           "offered_gbs": round(nbytes / arrivals[-1] / 1e9, 1),
+           "server": st_s, "plain_sequential": st_p,
+           "p99_speedup_vs_plain": round(st_p["p99_us"] / st_s["p99_us"], 2),
+           "int_results_equal_plain": bool(same),
+           "float_max_rel_diff_vs_plain": fdiff, "float_results_within_2e-5_of_plain": bool(fdiff <= 2e-5)}
+    out.update(served_fair(dev, pools))
     del pools
     torch.cuda.empty_cache()
-    return {"workload": "served regions: Poisson arrivals at %d/s for %.1f s (%d regions, %.1f GB), lengths "
-                        "log-uniform [2^8, 2^26], float32 (+comp) / int32 (+, max) / int64 (+, ^), "
-                        "resident pools, 64 GiB budget, 4 stream slots" % (rate, seconds, count, nbytes / 1e9),
-            "offered_gbs": round(nbytes / arrivals[-1] / 1e9, 1),
-            "server": st_s, "plain_sequential": st_p,
-            "p99_speedup_vs_plain": round(st_p["p99_us"] / st_s["p99_us"], 2),
-            "int_results_equal_plain": bool(same)}
+    return out
+
+
+def served_fair(dev, pools, equal_rate=25000.0, seconds=1.0, sat_server=60000, sat_plain=20000):
+    """The two arms at equal, sustainable load (an offered rate the plain arm
+    keeps up with), and each arm's saturation throughput (every region
+    arrives at time 0: regions/s over the whole drain)."""
+    from paper_1412_1127_gb300 import api
+    count = int(seconds * equal_rate)
+    regions, arrivals, nbytes, meta = served_requests(dev, pools, count, equal_rate, seed=7)
+    srv = api.Server(64 << 30, nstreams=4, max_batch=4096)
+    warm = min(2000, count)
+    srv.replay(regions[:warm], arrivals[:warm])
+    st_s = latency_stats(srv.replay(regions, arrivals), count)
+    api.accr_server_replay(None, regions[:warm], arrivals[:warm], plain=True)
+    st_p = latency_stats(api.accr_server_replay(None, regions, arrivals, plain=True), count)
+    regs_s, _, nb_s, _ = served_requests(dev, pools, sat_server, 1.0, seed=8)
+    res = srv.replay(regs_s, np.zeros(sat_server))
+    srv.destroy()
+    regs_p, _, nb_p, _ = served_requests(dev, pools, sat_plain, 1.0, seed=8)
+    resp = api.accr_server_replay(None, regs_p, np.zeros(sat_plain), plain=True)
+    sat_s, sat_p = latency_stats(res, sat_server), latency_stats(resp, sat_plain)
+    return {"equal_load": {"offered_regions_per_s": equal_rate, "regions": count,
+                           "offered_gbs": round(nbytes / arrivals[-1] / 1e9, 1),
+                           "server": st_s, "plain_sequential": st_p,
+                           "p50_speedup_vs_plain": round(st_p["p50_us"] / st_s["p50_us"], 2),
+                           "p99_speedup_vs_plain": round(st_p["p99_us"] / st_s["p99_us"], 2)},
+            "saturation": {"server_regions_per_s": sat_s["regions_per_s"], "server_regions": sat_server,
+                           "plain_regions_per_s": sat_p["regions_per_s"], "plain_regions": sat_plain,
+                           "server_gbs": round(nb_s / 1e9 * sat_s["regions_per_s"] / sat_server, 1),
+                           "plain_gbs": round(nb_p / 1e9 * sat_p["regions_per_s"] / sat_plain, 1),
+                           "throughput_ratio": round(sat_s["regions_per_s"] / sat_p["regions_per_s"], 2),
+                           "how": "every region arrives at time 0; regions/s from the first arrival to the last result"}}
 
 
 def served_sweep(dev, rates, seconds=1.0):
@@ -803,11 +846,25 @@ def measure_small_region(dev, n=1 << 20, reps=100):
     flushed, _, ahead2 = queued(lambda: (flush.fill_(1), region()))
     flush_only, _, ahead3 = queued(lambda: flush.fill_(1))
     cold = flushed - flush_only
+    # the C call alone (arguments marshalled once), and the launch floor: the
+    # same call on an empty region, and an empty kernel, back to back
+    arr, keep = api._clauses(cls)
+    L, xp, sp = api.lib(), x.data_ptr(), stream.cuda_stream
+    c_call = lambda: L.accr_reduce(xp, n, api.ACCR_I32, arr, 2, 0, sp)
+    warm_c, host_c_us, ahead4 = queued(c_call)
+    empty_region, _, ahead5 = queued(lambda: L.accr_reduce(xp, 0, api.ACCR_I32, arr, 2, 0, sp))
+    empty_kernel, _, ahead6 = queued(lambda: torch.cuda._sleep(0))
     return {"workload": "one region, 2^20 int32, + (int64 variable) and max in one pass",
             "warm": {"us_per_region": round(warm, 2), "gbs": round(4.0 * n / (warm * 1e-6) / 1e9, 1)},
+            "warm_c_call": {"us_per_region": round(warm_c, 2), "gbs": round(4.0 * n / (warm_c * 1e-6) / 1e9, 1)},
             "l2_flushed": {"us_per_region": round(cold, 2), "gbs": round(4.0 * n / (cold * 1e-6) / 1e9, 1)},
-            "host_us_per_call": round(host_us, 2), "queued_ahead": bool(ahead and ahead2 and ahead3),
-            "note": "back-to-back launches on one stream; the launch cadence of the stream is part of the time"}
+            "host_us_per_call": round(host_us, 2), "host_us_per_c_call": round(host_c_us, 2),
+            "empty_region_us": round(empty_region, 2), "empty_kernel_us": round(empty_kernel, 2),
+            "queued_ahead": bool(ahead and ahead2 and ahead3 and ahead4 and ahead5 and ahead6),
+            "note": "back-to-back launches on one stream, queued behind a long probe launch; empty_region is "
+                    "accr_reduce over n = 0 (the entry point's launch floor), empty_kernel a kernel that "
+                    "does nothing (the stream's launch cadence); host_us_per_call goes through the Python "
+                    "binding, host_us_per_c_call calls the C entry point with its arguments built once"}
 
 
 def measure_rows(dev, rows=65536, cols=4096, steps=10, warmup=3):
@@ -834,7 +891,7 @@ def measure_rows(dev, rows=65536, cols=4096, steps=10, warmup=3):
     nbytes = rows * cols * 4
     peaks, kind = measured_peaks()
     ok_max = bool(torch.equal(m, At.amax(dim=1)))
-    form = "split-row (each row cut into CTA tiles)" if cols * 4 >= (256 << 10) else "one warp per row"
+    form = "split-row (32 KiB chunks, warp runs, CTA merge)" if cols * 4 >= (256 << 10) else "one warp per row"
     return {"workload": "row sum + row max (one pass), %d x %d float U(-1,1)" % (rows, cols), "form": form,
             "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
             "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]), 4),

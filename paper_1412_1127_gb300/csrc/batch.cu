@@ -493,30 +493,6 @@ static int plan_from_segments(const void *values, const int64_t *off, int64_t ns
     return finish_plan(P);
 }
 
-// One region per row of a row-major matrix (row r starts r * ld elements in;
-// variable r of clause c at out_c + r).  The clauses are already lowered.
-static int plan_from_rows(const void *A, int64_t rows, int64_t cols, int64_t ld, int in_type, const ClauseDev *cl,
-                          int nc, HostPlan &P) {
-    if (rows > INT32_MAX / 2) return set_error(ACCR_EINVAL, "rowreduce: too many rows for the split-row path");
-    const int64_t eb = type_bytes(in_type);
-    P.regions.clear();
-    P.regions.reserve((size_t)rows * (nc > 2 ? 2 : 1));
-    for (int64_t r = 0; r < rows; ++r) {
-        RegionDev d;
-        memset(&d, 0, sizeof d);
-        d.in = (const char *)A + r * ld * eb;
-        d.n = cols;
-        d.in_type = in_type;
-        d.nc = nc;
-        for (int c = 0; c < nc; ++c) {
-            d.cl[c] = cl[c];
-            d.cl[c].out = (char *)cl[c].out + r * type_bytes(cl[c].acc_type);
-        }
-        push_split(P.regions, d);
-    }
-    return finish_plan(P);
-}
-
 static int batch_grid(const HostPlan &P) {
     static std::mutex mu;
     static int cached[64] = {0};
@@ -671,15 +647,6 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
     if (rc != ACCR_OK) return rc;
     if (flags & ACCR_SYNC) return cuda_check(cudaStreamSynchronize(s), "batch: sync");
     return ACCR_OK;
-}
-
-int batch_launch_rows(const void *A, int64_t rows, int64_t cols, int64_t ld, int in_type, const ClauseDev *cl, int nc,
-                      int64_t tile_bytes, accr_stream_t stream) {
-    HostPlan P;
-    P.tile_override = tile_bytes;
-    int rc = plan_from_rows(A, rows, cols, ld, in_type, cl, nc, P);
-    if (rc != ACCR_OK) return rc;
-    return run_once(P, 0, stream);
 }
 
 int batch_launch_regions(const accr_region *regions, int64_t nregions, accr_stream_t stream, int64_t tile_bytes) {

@@ -1,5 +1,5 @@
-// batch.cuh -- internal entries of the batched-region path for other parts of
-// the library (the served request loop, the row nest's split-row path).
+// batch.cuh -- internal entry of the batched-region path for other parts of
+// the library (the served request loop).
 #pragma once
 
 #include "common.cuh"
@@ -11,9 +11,4 @@ namespace accr {
 // process-wide tiling (accr_batch_tiling); the split of a region still
 // depends only on its own type and length.
 int batch_launch_regions(const accr_region *regions, int64_t nregions, accr_stream_t stream, int64_t tile_bytes = 0);
-// The rows of a row-major matrix as regions of one batch (row r: cols
-// elements from A + r * ld; variable r of clause c at cl[c].out + r), cut into
-// tiles of tile_bytes (the row nest's split-row path).
-int batch_launch_rows(const void *A, int64_t rows, int64_t cols, int64_t ld, int in_type, const ClauseDev *cl, int nc,
-                      int64_t tile_bytes, accr_stream_t stream);
 }  // namespace accr

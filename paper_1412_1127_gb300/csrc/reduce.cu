@@ -13,6 +13,7 @@
 // on the CPU, Sec. 4.2 on SRAD) is kept behind ACCR_TWO_LEVEL_HOST.
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 
@@ -163,21 +164,23 @@ __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ R
 
 // ---- host side -------------------------------------------------------------------
 
+// Resident-grid size per device, computed once (a racing first computation
+// stores the same value twice); read without a lock.
 template <typename T, int NC>
 static int occupancy_grid() {
-    static std::mutex mu;
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];
     const DeviceInfo &d = device_info();
-    std::lock_guard<std::mutex> lk(mu);
-    int &slot = cached[d.id & 63];
-    if (!slot) {
+    std::atomic<int> &slot = cached[d.id & 63];
+    int g = slot.load(std::memory_order_relaxed);
+    if (!g) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_kernel<T, NC>, RB, 0);
         if (per_sm < 1) per_sm = 1;
-        slot = per_sm * d.sms;
-        if (slot > kMaxGrid) slot = kMaxGrid;
+        g = per_sm * d.sms;
+        if (g > kMaxGrid) g = kMaxGrid;
+        slot.store(g, std::memory_order_relaxed);
     }
-    return slot;
+    return g;
 }
 
 template <typename T, int NC, int W0 = -1, int W1 = -1>

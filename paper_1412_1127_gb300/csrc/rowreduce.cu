@@ -2,51 +2,63 @@
 // one reduction variable per row of a row-major matrix (the two-level loop
 // shape of Listing 1a with an inner reduction; IPMACC Sec. 1.3, Stage 3.4).
 //
-// Mapping: gang -> CTA, worker -> warp, vector -> lane.  Two forms, chosen by
-// the row's length alone (so a row's result never depends on how many rows
-// the matrix has):
+// Mapping: gang -> CTA, worker -> warp, vector -> lane.  A warp folds one
+// stretch of a row at a time: lanes stream it in 16-byte vectors (RU2 in
+// flight per lane) and merge through shuffles.  Stretches whose start is not
+// 16-byte aligned (ld not a multiple of the vector) fold their head and tail
+// element by element.  Two forms, chosen by the row's length alone, so a
+// row's result never depends on how many rows the matrix has:
 //
-//   * rows shorter than SPLIT_ROW_BYTES: one warp owns a row, so no
-//     cross-warp or cross-gang merge is needed: lanes stream the row in
-//     16-byte vectors (RU2 in flight per lane), merge through shuffles, and
-//     lane 0 writes the row's variable.  Rows whose start is not 16-byte
-//     aligned (ld not a multiple of the vector) fold their head and tail
-//     element by element.
-//   * longer rows: each row is a region of one batched launch (batch.cu),
-//     cut into CTA tiles of split_tile_bytes(row bytes) (at least 256 tiles a
-//     row up to 2 MiB tiles); a tile's partial goes to scratch and the row's
-//     last tile merges the partials in tile order.  A few long rows then
-//     spread over every SM instead of over a few warps.
+//   * rows shorter than SPLIT_ROW_BYTES: the stretch is the whole row and
+//     lane 0 writes the row's variable; no cross-warp merge at all.
+//   * longer rows: the stretch is one of the row's SPLIT_CHUNK_BYTES chunks
+//     (a few long rows then spread over every SM instead of a few warps).
+//     Each resident warp takes a contiguous run of chunks (the same number
+//     for every warp, to within the last run) and lane 0 stores each chunk's
+//     partial in the chunk's own slot; when its eight warps are done the CTA
+//     counts its chunks into each row it touched, and the CTA whose count
+//     completes a row merges the row's partials in chunk order (thread t
+//     takes chunks t, t + 256, ..., four loads in flight, then the CTA's
+//     shuffle and shared-memory tree) and writes the variable.  The partial
+//     slots and the merge order depend on the row length only, not on which
+//     warp folded which chunk.
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 
-#include "batch.cuh"
 #include "common.cuh"
 #include "fold.cuh"
 
 namespace accr {
 
-constexpr int64_t SPLIT_ROW_BYTES = 256 * 1024;
-
-// Tile of the split-row form: row bytes / 256 rounded down to a power of two,
-// within [64 KiB, 2 MiB].
-static int64_t split_tile_bytes(int64_t row_bytes) {
-    int64_t t = 64 * 1024;
-    while (t * 2 <= row_bytes / 256 && t < 2 * 1024 * 1024) t *= 2;
-    return t;
-}
 
 constexpr int WB = 256;  // threads per CTA (8 warps = 8 rows in flight)
 constexpr int RU2 = 8;   // 16-byte vectors per lane per iteration
+constexpr int64_t SPLIT_ROW_BYTES = 256 * 1024;
+constexpr int64_t SPLIT_CHUNK_BYTES = 32 * 1024;
 
 struct RowArgs {
     const void *A;
     int64_t rows, cols, ld;
     int nc;
     ClauseDev cl[ACCR_MAX_CLAUSES];
+    int64_t chunk;        // split form: elements per chunk
+    int64_t cpr;          // split form: chunks per row
+    int64_t per_warp;     // split form: chunks of each warp's contiguous run
+    Partial *partials;    // split form: [rows][nc][cpr]
+    unsigned *counters;   // split form: [rows], zero on entry, zero again on exit
 };
+
+__device__ __forceinline__ Partial ld_row_partial(const Partial *p) {
+    uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
+    Partial q;
+    q.a = ((uint64_t)v.y << 32) | v.x;
+    q.c = __uint_as_float(v.z);
+    q.pad = 0;
+    return q;
+}
 
 __device__ __forceinline__ uint4 ld_row(const uint4 *p) {
     uint4 v;
@@ -56,95 +68,197 @@ __device__ __forceinline__ uint4 ld_row(const uint4 *p) {
     return v;
 }
 
-// W0 / W1 >= 0 fix the working codes of clauses 0 / 1 at compile time (the
-// fold's operator switch then disappears from the row loop); -1 reads them
-// from the arguments.
-template <typename T, int NC, int W0 = -1, int W1 = -1>
-__global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ RowArgs p) {
+// One stretch of a row (elements [lo, lo + len) of row r), folded by one
+// warp and merged across its lanes.
+template <typename T, int NC>
+__device__ __forceinline__ void fold_stretch(const RowArgs &p, const int (&w)[NC], int64_t r, int64_t lo, int64_t len,
+                                             int lane, Acc (&A)[NC]) {
     constexpr bool E64 = sizeof(T) == 8;
     constexpr int EPV = 16 / (int)sizeof(T);
+    const T *row = (const T *)p.A + r * p.ld + lo;
+    const int64_t mis = (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) / sizeof(T));
+    const int64_t head = mis < len ? mis : len;
+    const uint4 *vr = (const uint4 *)(row + head);
+    const int64_t nvec = (len - head) / EPV;
+    const int64_t tail0 = head + nvec * EPV;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        A[c].a = p.cl[c].ident;
+        A[c].c = 0.f;
+    }
+    if (lane < head) {
+        T x = row[lane];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) fold_one<T>(w[c], A[c], x);
+    }
+    if (tail0 + lane < len) {
+        T x = row[tail0 + lane];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) fold_one<T>(w[c], A[c], x);
+    }
+    int64_t v = lane;
+    for (; v + (RU2 - 1) * 32 < nvec; v += 32 * RU2) {
+        uint4 b[RU2];
+#pragma unroll
+        for (int u = 0; u < RU2; ++u) b[u] = ld_row(vr + v + u * 32);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) fold_vec<T, RU2>(w[c], A[c], b);
+    }
+#pragma unroll
+    for (int u = 0; u < RU2; ++u) {
+        const int64_t vv = v + u * 32;
+        if (vv < nvec) {
+            uint4 b = ld_row(vr + vv);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) fold_vec<T, 1>(w[c], A[c], &b);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) warp_merge(w[c], E64, A[c]);
+}
+
+// W0 / W1 >= 0 fix the working codes of clauses 0 / 1 at compile time (the
+// fold's operator switch then disappears from the row loop); -1 reads them
+// from the arguments.  SPLIT selects the chunked form for long rows.
+template <typename T, int NC, int W0 = -1, int W1 = -1, bool SPLIT = false>
+__global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ RowArgs p) {
+    constexpr bool E64 = sizeof(T) == 8;
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (WB / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (WB / 32) + (threadIdx.x >> 5);
     const int64_t cols = p.cols;
     int w[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = (c == 0 && W0 >= 0) ? W0 : (c == 1 && W1 >= 0) ? W1 : p.cl[c].wcode;
+    Acc A[NC];
 
-    for (int64_t r = (int64_t)blockIdx.x * (WB / 32) + (threadIdx.x >> 5); r < p.rows; r += warps) {
-        const T *row = (const T *)p.A + r * p.ld;
-        const int64_t mis = (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) / sizeof(T));
-        const int64_t head = mis < cols ? mis : cols;
-        const uint4 *vr = (const uint4 *)(row + head);
-        const int64_t nvec = (cols - head) / EPV;
-        const int64_t tail0 = head + nvec * EPV;
-        Acc A[NC];
+    if (!SPLIT) {
+        const int64_t warps = (int64_t)gridDim.x * (WB / 32);
+        for (int64_t r = gw; r < p.rows; r += warps) {
+            fold_stretch<T, NC>(p, w, r, 0, cols, lane, A);
+            if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            A[c].a = p.cl[c].ident;
-            A[c].c = 0.f;
-        }
-        if (lane < head) {
-            T x = row[lane];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) fold_one<T>(w[c], A[c], x);
-        }
-        if (tail0 + lane < cols) {
-            T x = row[tail0 + lane];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) fold_one<T>(w[c], A[c], x);
-        }
-        int64_t v = lane;
-        for (; v + (RU2 - 1) * 32 < nvec; v += 32 * RU2) {
-            uint4 b[RU2];
-#pragma unroll
-            for (int u = 0; u < RU2; ++u) b[u] = ld_row(vr + v + u * 32);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) fold_vec<T, RU2>(w[c], A[c], b);
-        }
-#pragma unroll
-        for (int u = 0; u < RU2; ++u) {
-            const int64_t vv = v + u * 32;
-            if (vv < nvec) {
-                uint4 b = ld_row(vr + vv);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) fold_vec<T, 1>(w[c], A[c], &b);
+                for (int c = 0; c < NC; ++c)
+                    store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, to_final(w[c], A[c])));
             }
         }
+        return;
+    }
+    // chunks k0 .. k1-1 (a contiguous run) of the rows x cpr chunks; the
+    // CTA's eight runs are contiguous too
+    __shared__ Acc sh[NC][WB / 32];
+    __shared__ int s_last;
+    const int64_t total = p.rows * p.cpr;
+    const int64_t k0 = gw * p.per_warp;
+    const int64_t k1 = (k0 + p.per_warp) < total ? (k0 + p.per_warp) : total;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int64_t r = k / p.cpr, j = k - r * p.cpr, lo = j * p.chunk;
+        fold_stretch<T, NC>(p, w, r, lo, (cols - lo) < p.chunk ? (cols - lo) : p.chunk, lane, A);
+        if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            warp_merge(w[c], E64, A[c]);
-            if (lane == 0) store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, to_final(w[c], A[c])));
+            for (int c = 0; c < NC; ++c) {
+                Partial q;
+                q.a = A[c].a;
+                q.c = A[c].c;
+                q.pad = 0;
+                p.partials[(r * NC + c) * p.cpr + j] = q;
+            }
         }
+    }
+    // the CTA counts its chunks into each row it touched; the CTA whose count
+    // completes a row merges the row's partials in chunk order (thread t takes
+    // chunks t, t + WB, ..., four loads in flight, then the CTA tree)
+    const int64_t c0 = (int64_t)blockIdx.x * (WB / 32) * p.per_warp;
+    const int64_t c1 = (c0 + (WB / 32) * p.per_warp) < total ? (c0 + (WB / 32) * p.per_warp) : total;
+    __syncthreads();
+    if (c0 >= total) return;  // uniform across the CTA
+    for (int64_t r = c0 / p.cpr; r <= (c1 - 1) / p.cpr; ++r) {
+        const int64_t a = (r * p.cpr > c0 ? r * p.cpr : c0), b = ((r + 1) * p.cpr < c1 ? (r + 1) * p.cpr : c1);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = (atomicAdd(&p.counters[r], (unsigned)(b - a)) + (unsigned)(b - a)) == (unsigned)p.cpr;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            int fw[NC];
+            uint64_t fid[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                fw[c] = final_code(w[c]);
+                fid[c] = final_ident(p.cl[c]);
+                A[c].a = fid[c];
+                A[c].c = 0.f;
+                const Partial *pp = &p.partials[(r * NC + c) * p.cpr];
+                for (int64_t b0 = threadIdx.x; b0 < p.cpr; b0 += WB * 4) {
+                    Partial q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (b0 + u * WB < p.cpr) q[u] = ld_row_partial(pp + b0 + u * WB);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (b0 + u * WB < p.cpr) {
+                            Acc Q;
+                            Q.a = q[u].a;
+                            Q.c = q[u].c;
+                            merge(fw[c], E64, A[c], to_final(w[c], Q));
+                        }
+                    }
+                }
+            }
+            cta_merge<NC, WB>(fw, fid, E64, A, sh);
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, A[c]));
+                p.counters[r] = 0u;
+            }
+        }
+        __syncthreads();
     }
 }
 
-template <typename T, int NC, int W0 = -1, int W1 = -1>
-static int row_grid(int64_t rows) {
-    static std::mutex mu;
-    static int cached[64] = {0};
+template <typename T, int NC, int W0, int W1, bool SPLIT>
+static int max_row_grid() {
+    static std::atomic<int> cached[64];
     const DeviceInfo &d = device_info();
-    int maxg;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        int &slot = cached[d.id & 63];
-        if (!slot) {
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowreduce_kernel<T, NC, W0, W1>, WB, 0);
-            if (per_sm < 1) per_sm = 1;
-            slot = per_sm * d.sms;
-        }
-        maxg = slot;
+    std::atomic<int> &slot = cached[d.id & 63];
+    int g = slot.load(std::memory_order_relaxed);
+    if (!g) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowreduce_kernel<T, NC, W0, W1, SPLIT>, WB, 0);
+        if (per_sm < 1) per_sm = 1;
+        g = per_sm * d.sms;
+        slot.store(g, std::memory_order_relaxed);
     }
-    int64_t want = (rows + WB / 32 - 1) / (WB / 32);
-    if (want < 1) want = 1;
-    return (int)(want < maxg ? want : maxg);
+    return g;
+}
+
+// Warps for `segs` stretches: rows (one warp per row, at most the resident
+// grid, the rest in later rounds), or chunks of long rows (the resident warps,
+// each taking a contiguous run of the same number of chunks, to within the
+// last run).  Returns the CTA count; `per_warp` gets the run length.
+template <typename T, int NC, int W0, int W1, bool SPLIT>
+static int row_grid(int64_t segs, int64_t *per_warp) {
+    const int64_t maxw = (int64_t)max_row_grid<T, NC, W0, W1, SPLIT>() * (WB / 32);
+    int64_t wantw = segs < maxw ? segs : maxw;
+    if (wantw < 1) wantw = 1;
+    if (SPLIT) {
+        *per_warp = (segs + wantw - 1) / wantw;
+        wantw = (segs + *per_warp - 1) / *per_warp;
+    }
+    const int64_t g = (wantw + WB / 32 - 1) / (WB / 32);
+    return (int)(g < 1 ? 1 : g);
 }
 
 template <typename T, int NC, int W0 = -1, int W1 = -1>
 static int row_launch_t(RowArgs &a, cudaStream_t s) {
     int rc = launch_guard("rowreduce_kernel");
     if (rc != ACCR_OK) return rc;
-    rowreduce_kernel<T, NC, W0, W1><<<row_grid<T, NC, W0, W1>(a.rows), WB, 0, s>>>(a);
+    if (a.cpr > 0) {
+        const int g = row_grid<T, NC, W0, W1, true>(a.rows * a.cpr, &a.per_warp);
+        rowreduce_kernel<T, NC, W0, W1, true><<<g, WB, 0, s>>>(a);
+    } else {
+        rowreduce_kernel<T, NC, W0, W1, false><<<row_grid<T, NC, W0, W1, false>(a.rows, nullptr), WB, 0, s>>>(a);
+    }
     return launched("rowreduce_kernel");
 }
 
@@ -212,15 +326,22 @@ extern "C" ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols
     if (((uintptr_t)A % (uintptr_t)type_bytes(in_type)) != 0)
         return set_error(ACCR_EINVAL, "accr_rowreduce: A is not aligned to its element size");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t row_bytes = cols * (int64_t)type_bytes(in_type);
-    if (row_bytes >= SPLIT_ROW_BYTES) {
-        rc = batch_launch_rows(A, rows, cols, ld, in_type, cl, nclauses, split_tile_bytes(row_bytes), stream);
-        if (rc != ACCR_OK) return rc;
-        if (flags & ACCR_SYNC) return cuda_check(cudaStreamSynchronize(s), "accr_rowreduce: sync");
-        return ACCR_OK;
-    }
     RowArgs a;
     memset(&a, 0, sizeof a);
+    const int64_t eb = type_bytes(in_type), row_bytes = cols * eb;
+    if (row_bytes >= SPLIT_ROW_BYTES) {
+        // chunked form: partials [rows][nclauses][cpr] and one counter per row
+        a.chunk = SPLIT_CHUNK_BYTES / eb;
+        a.cpr = (cols + a.chunk - 1) / a.chunk;
+        const size_t pbytes = (size_t)rows * (size_t)nclauses * (size_t)a.cpr * sizeof(Partial);
+        const size_t cbytes = (size_t)rows * sizeof(unsigned);
+        Scratch *scr = scratch_for(stream, pbytes + 256 + cbytes);
+        if (!scr) return ACCR_ENOMEM;
+        a.partials = (Partial *)scr->buf;
+        a.counters = (unsigned *)((char *)scr->buf + ((pbytes + 255) & ~(size_t)255));
+        rc = cuda_check(cudaMemsetAsync(a.counters, 0, cbytes, s), "accr_rowreduce: clear row counters");
+        if (rc != ACCR_OK) return rc;
+    }
     a.A = A;
     a.rows = rows;
     a.cols = cols;

@@ -65,16 +65,28 @@ static std::map<int, DeviceInfo> g_dev;
 const DeviceInfo &device_info() {
     int dev = 0;
     cudaGetDevice(&dev);
+    // per-thread memo of the last device (map entries never move): no lock on
+    // the launch path of a thread that keeps to one device
+    static thread_local int t_dev = -1;
+    static thread_local const DeviceInfo *t_info = nullptr;
+    if (dev == t_dev) return *t_info;
     std::lock_guard<std::mutex> lk(g_dev_mu);
-    auto it = g_dev.find(dev);
-    if (it != g_dev.end()) return it->second;
+    auto hit = g_dev.find(dev);
+    if (hit != g_dev.end()) {
+        t_dev = dev;
+        t_info = &hit->second;
+        return hit->second;
+    }
     DeviceInfo d{};
     d.id = dev;
     cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&d.l2_bytes, cudaDevAttrL2CacheSize, dev);
     cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (d.sms <= 0) d.sms = 1;
-    return g_dev.emplace(dev, d).first->second;
+    const DeviceInfo &ref = g_dev.emplace(dev, d).first->second;
+    t_dev = dev;
+    t_info = &ref;
+    return ref;
 }
 
 // ---- scratch -----------------------------------------------------------------
@@ -82,6 +94,7 @@ struct ScratchEntry {
     Scratch s{};
     void *host = nullptr;
     size_t host_bytes = 0;
+    std::atomic<uint64_t> gen{0};  // bumped whenever `s` is replaced
 };
 static std::mutex g_scr_mu;
 static std::map<std::pair<int, uintptr_t>, ScratchEntry *> g_scr;
@@ -97,10 +110,34 @@ static ScratchEntry *entry_for(accr_stream_t stream) {
     return e;
 }
 
+// Per-thread memo of the last (device, stream) scratch: a repeated call on the
+// same stream takes no lock unless the scratch was replaced meanwhile.
+struct ScratchMemo {
+    int dev = -1;
+    accr_stream_t stream = nullptr;
+    ScratchEntry *e = nullptr;
+    uint64_t gen = 0;
+    size_t bytes = 0;
+};
+static thread_local ScratchMemo t_scr;
+
 Scratch *scratch_for(accr_stream_t stream, size_t bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (t_scr.e && t_scr.dev == dev && t_scr.stream == stream && bytes <= t_scr.bytes &&
+        t_scr.e->gen.load(std::memory_order_acquire) == t_scr.gen)
+        return &t_scr.e->s;
     std::lock_guard<std::mutex> lk(g_scr_mu);
     ScratchEntry *e = entry_for(stream);
-    if (e->s.counters && e->s.bytes >= bytes) return &e->s;
+    auto remember = [&] {
+        t_scr.dev = dev;
+        t_scr.stream = stream;
+        t_scr.e = e;
+        t_scr.gen = e->gen.load(std::memory_order_relaxed);
+        t_scr.bytes = e->s.bytes;
+        return &e->s;
+    };
+    if (e->s.counters && e->s.bytes >= bytes) return remember();
     if (fault_take(ACCR_FAULT_ALLOC)) {
         set_error(ACCR_ENOMEM, "scratch: injected allocation failure");
         return nullptr;
@@ -112,6 +149,7 @@ Scratch *scratch_for(accr_stream_t stream, size_t bytes) {
             return nullptr;
         cudaFree(e->s.counters);
         e->s = Scratch{};
+        e->gen.fetch_add(1, std::memory_order_release);
     }
     size_t want = bytes < (1u << 20) ? (1u << 20) : bytes;
     want = (want + 4095) & ~(size_t)4095;
@@ -129,7 +167,8 @@ Scratch *scratch_for(accr_stream_t stream, size_t bytes) {
     e->s.counters = (unsigned *)p;
     e->s.buf = (char *)p + head;
     e->s.bytes = want;
-    return &e->s;
+    e->gen.fetch_add(1, std::memory_order_release);
+    return remember();
 }
 
 void *host_staging_for(accr_stream_t stream, size_t bytes) {
