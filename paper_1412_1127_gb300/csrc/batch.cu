@@ -22,8 +22,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
 #include <map>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -42,15 +46,18 @@ constexpr int BB = 256;  // threads per CTA (4 CTAs per SM: one CTA's merge betw
 constexpr int BU = 4;    // 16-byte vectors per thread per iteration (tiles)
 constexpr int SU = 8;    // 16-byte vectors per lane per iteration (warp regions)
 
+// A region's descriptor carries at most two clauses: a region with three or
+// four is planned as two descriptors over the same elements.
+constexpr int RD_CLAUSES = 2;
 struct RegionDev {
     const void *in;
     int64_t n;
     int64_t tile0;  // first tile of a tiled region; -1 for a warp region
     int32_t in_type;
-    int32_t nc;
-    ClauseDev cl[ACCR_MAX_CLAUSES];
+    int32_t nc;     // 1 or 2
+    ClauseDev cl[RD_CLAUSES];
 };
-static_assert(sizeof(RegionDev) == 192, "RegionDev layout");
+static_assert(sizeof(RegionDev) == 112, "RegionDev layout");
 
 struct BatchArgs {
     const RegionDev *regions;
@@ -58,7 +65,7 @@ struct BatchArgs {
     const int32_t *small;        // [S] warp regions, in queue order
     int64_t T, S;
     int64_t tile_bytes;
-    Partial *partials;           // [sum of tiles][ACCR_MAX_CLAUSES], slot tile0 + k
+    Partial *partials;           // [sum of tiles][RD_CLAUSES], slot tile0 + k
     unsigned *counters;          // [R] tiles done per region; zero on entry and exit
     unsigned *queue;             // [3] next tile, next warp region, CTAs done
 };
@@ -154,7 +161,7 @@ __device__ __noinline__ void tile_fold(const BatchArgs &p, const RegionDev *d, i
             q.a = A[c].a;
             q.c = A[c].c;
             q.pad = 0;
-            p.partials[t * ACCR_MAX_CLAUSES + c] = q;
+            p.partials[t * RD_CLAUSES + c] = q;
         }
         __threadfence();
         const unsigned old = atomicAdd(&p.counters[r], 1u);
@@ -174,7 +181,7 @@ __device__ __noinline__ void tile_fold(const BatchArgs &p, const RegionDev *d, i
         A[c].a = fid[c];
         A[c].c = 0.f;
         for (int64_t j = threadIdx.x; j < ntiles; j += BB) {
-            Partial q = ld_partial_cg(&p.partials[(tile0 + j) * ACCR_MAX_CLAUSES + c]);
+            Partial q = ld_partial_cg(&p.partials[(tile0 + j) * RD_CLAUSES + c]);
             Acc Q;
             Q.a = q.a;
             Q.c = q.c;
@@ -259,7 +266,7 @@ __device__ __noinline__ void warp_fold(const RegionDev *d, int lane) {
 
 __device__ __forceinline__ void batch_body(const BatchArgs &p, const RegionDev *regions, const int2 *tiles,
                                            const int32_t *small) {
-    __shared__ Acc sh[ACCR_MAX_CLAUSES][BB / 32];
+    __shared__ Acc sh[RD_CLAUSES][BB / 32];
     __shared__ int s_last;
     __shared__ long long s_q;
     // tiles of long regions, one CTA per tile, taken from a queue (largest
@@ -342,124 +349,390 @@ struct HostPlan {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static int log2_floor(uint64_t v) {
-    int b = 0;
-    while (v >>= 1) ++b;
-    return b;
+// The calling thread's plan for one-shot batches: its vectors keep their
+// capacity from call to call, so planning a batch of the same size again
+// allocates nothing and touches no new pages.
+static HostPlan &thread_plan(int64_t tile_override) {
+    static thread_local HostPlan P;
+    P.tile_override = tile_override;
+    return P;
 }
 
-// Assigns each region to the warp list or to tiles, by its own type and
-// length, and orders both queues: grouped by (element type, clause count) so
-// that neighbouring work runs the same code, largest first within a group so
-// that the small pieces fill in at the end.  (Counting sort on a size bucket.)
-static int finish_plan(HostPlan &P) {
-    const int64_t small_b = g_small_bytes.load(), tile_b = P.tile_override > 0 ? P.tile_override : g_tile_bytes.load();
-    P.tile_bytes = tile_b;
-    P.tiles.clear();
-    P.small.clear();
-    const int64_t R = (int64_t)P.regions.size();
-    constexpr int NKEY = 8 * 64;
-    std::vector<int64_t> tile_count(NKEY + 1, 0), small_count(NKEY + 1, 0);
-    int64_t slots = 0;
-    auto key_of = [](const RegionDev &d, int64_t bytes) {
-        const int group = d.in_type * 2 + (d.nc - 1);
-        return group * 64 + (63 - log2_floor((uint64_t)(bytes > 0 ? bytes : 1)));
+static int log2_floor(uint64_t v) { return v ? 63 - __builtin_clzll(v) : 0; }
+
+// ---- host: planner threads ----------------------------------------------------------
+//
+// Planning a batch of many regions (lowering each region's clauses, sorting
+// the work queues, writing the plan into pinned staging) takes a few hundred
+// microseconds on one host core for 20,000 regions, longer than the batch's
+// kernel.  Large plans are therefore cut into contiguous ranges of regions that
+// a small pool of host threads plans in parallel; the result is the same plan,
+// entry for entry, as the serial one.
+class PlanPool {
+public:
+    explicit PlanPool(int workers) {
+        for (int i = 0; i < workers; ++i) th_.emplace_back([this] { loop(); });
+    }
+    ~PlanPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (std::thread &t : th_) t.join();
+    }
+    int threads() const { return (int)th_.size() + 1; }
+    // Runs f(0) .. f(n - 1) on the pool's threads and the caller's; returns
+    // when all have finished.  One job at a time.
+    void run(int n, const std::function<void(int)> &f) {
+        std::lock_guard<std::mutex> one(run_mu_);
+        Job j;
+        j.fn = &f;
+        j.n = n;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            cur_ = &j;
+            ++gen_;
+        }
+        cv_.notify_all();
+        const int mine = work(j);
+        std::unique_lock<std::mutex> lk(mu_);
+        cur_ = nullptr;  // no thread attaches to this job any more
+        j.done += mine;
+        done_cv_.wait(lk, [&] { return j.done == j.n && j.active == 0; });
+    }
+
+private:
+    struct Job {
+        const std::function<void(int)> *fn = nullptr;
+        int n = 0;
+        std::atomic<int> next{0};
+        int done = 0;    // items finished (under mu_)
+        int active = 0;  // pool threads attached (under mu_)
     };
-    for (int64_t r = 0; r < R; ++r) {
-        RegionDev &d = P.regions[r];
-        const int64_t eb = type_bytes(d.in_type);
-        if (d.n * eb <= small_b) {
-            d.tile0 = -1;
-            small_count[key_of(d, d.n * eb) + 1]++;
-        } else {
-            const int64_t te = tile_b / eb;
-            const int64_t nt = (d.n + te - 1) / te;
-            d.tile0 = slots;
-            slots += nt;
-            if (slots > INT32_MAX) return set_error(ACCR_EINVAL, "batch: more than 2^31 tiles");
-            tile_count[key_of(d, tile_b) + 1] += nt - 1;
-            tile_count[key_of(d, (d.n - (nt - 1) * te) * eb) + 1]++;
+    static int work(Job &j) {
+        int mine = 0;
+        for (int i = j.next.fetch_add(1); i < j.n; i = j.next.fetch_add(1)) {
+            (*j.fn)(i);
+            ++mine;
+        }
+        return mine;
+    }
+    void loop() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            Job *j = cur_;
+            if (!j) continue;
+            ++j->active;
+            lk.unlock();
+            const int mine = work(*j);
+            lk.lock();
+            j->done += mine;
+            --j->active;
+            done_cv_.notify_all();
         }
     }
-    for (int k = 0; k < NKEY; ++k) {
-        tile_count[k + 1] += tile_count[k];
-        small_count[k + 1] += small_count[k];
-    }
-    P.ntiles = slots;
-    P.tiles.resize((size_t)tile_count[NKEY]);
-    P.small.resize((size_t)small_count[NKEY]);
-    for (int64_t r = 0; r < R; ++r) {
-        const RegionDev &d = P.regions[r];
-        const int64_t eb = type_bytes(d.in_type);
-        if (d.tile0 < 0) {
-            P.small[(size_t)small_count[key_of(d, d.n * eb)]++] = (int32_t)r;
-        } else {
-            const int64_t te = tile_b / eb;
-            const int64_t nt = (d.n + te - 1) / te;
-            const int kfull = key_of(d, tile_b), klast = key_of(d, (d.n - (nt - 1) * te) * eb);
-            for (int64_t k = 0; k < nt; ++k)
-                P.tiles[(size_t)tile_count[k + 1 < nt ? kfull : klast]++] = make_int2((int)r, (int)k);
-        }
-    }
-    P.off_tiles = align_up(sizeof(RegionDev) * (size_t)R, 256);
-    P.off_small = align_up(P.off_tiles + sizeof(int2) * P.tiles.size(), 256);
-    P.plan_bytes = P.off_small + 4 * P.small.size();
-    P.off_partials = align_up(P.plan_bytes, 256);
-    P.total_bytes = P.off_partials + sizeof(Partial) * ACCR_MAX_CLAUSES * (size_t)P.ntiles + 256;
-    return ACCR_OK;
+    std::vector<std::thread> th_;
+    std::mutex run_mu_, mu_;
+    std::condition_variable cv_, done_cv_;
+    Job *cur_ = nullptr;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+constexpr int64_t PAR_MIN_REGIONS = 4096;  // smaller plans stay on the calling thread
+constexpr int PLAN_THREADS = 4;            // pool threads besides the caller
+
+static PlanPool &plan_pool() {
+    static PlanPool *pool = new PlanPool(PLAN_THREADS);  // lives until exit
+    return *pool;
 }
 
-static void write_plan(const HostPlan &P, char *dst) {
-    memcpy(dst, P.regions.data(), sizeof(RegionDev) * P.regions.size());
-    if (!P.tiles.empty()) memcpy(dst + P.off_tiles, P.tiles.data(), sizeof(int2) * P.tiles.size());
-    if (!P.small.empty()) memcpy(dst + P.off_small, P.small.data(), 4 * P.small.size());
+// Runs f over `chunks` chunks: in the pool if the plan is large, else here.
+static void plan_for(int64_t R, int chunks, const std::function<void(int)> &f) {
+    if (chunks <= 1 || R < PAR_MIN_REGIONS) {
+        for (int c = 0; c < chunks; ++c) f(c);
+        return;
+    }
+    plan_pool().run(chunks, f);
 }
 
 static int check_region_ptr(const void *in, int64_t n, int t, int64_t r) {
     if (n < 0) return set_error(ACCR_EINVAL, "region %lld: n < 0", (long long)r);
     if (n > 0 && !in) return set_error(ACCR_EINVAL, "region %lld: in is NULL", (long long)r);
-    if (((uintptr_t)in % (uintptr_t)type_bytes(t)) != 0)
+    if (((uintptr_t)in & (uintptr_t)(type_bytes(t) - 1)) != 0)
         return set_error(ACCR_EINVAL, "region %lld: in is not aligned to its element size", (long long)r);
     return ACCR_OK;
 }
 
-// Appends a region's descriptor; one with three or four clauses becomes two
-// descriptors over the same elements (clauses 0-1 and 2-3).
-static void push_split(std::vector<RegionDev> &out, const RegionDev &d) {
-    if (d.nc <= 2) {
-        out.push_back(d);
-        return;
+// Lowered clauses of recent region kinds, reused when a region has the same
+// element type, flags, operators, variable types and prior values as one of
+// them (only the outputs then differ): batches are usually many regions of a
+// few kinds, and lowering dominated the host cost of a plan.
+struct ClauseMemo {
+    struct Entry {
+        bool valid = false;
+        int in_type = 0, nc = 0;
+        unsigned flags = 0;
+        int op[ACCR_MAX_CLAUSES], acc[ACCR_MAX_CLAUSES];
+        const void *init[ACCR_MAX_CLAUSES];
+        ClauseDev dev[ACCR_MAX_CLAUSES];
+        bool same(const accr_region &g) const {
+            if (!valid || g.in_type != in_type || g.nclauses != nc || g.flags != flags) return false;
+            for (int c = 0; c < nc; ++c)
+                if (g.clauses[c].op != op[c] || g.clauses[c].acc_type != acc[c] || g.clauses[c].init != init[c])
+                    return false;
+            return true;
+        }
+    };
+    Entry e[4];
+    int next = 0;
+};
+
+static int lower_region(const accr_region &g, int64_t r, ClauseMemo &m, ClauseDev *cl) {
+    for (const ClauseMemo::Entry &x : m.e) {
+        if (!x.same(g)) continue;
+        for (int c = 0; c < x.nc; ++c) {
+            if (!g.clauses[c].out) return set_error(ACCR_EINVAL, "region %lld: clause %d: out is NULL", (long long)r, c);
+            cl[c] = x.dev[c];
+            cl[c].out = g.clauses[c].out;
+        }
+        return ACCR_OK;
     }
-    RegionDev a = d, b = d;
-    a.nc = 2;
-    b.nc = d.nc - 2;
-    b.cl[0] = d.cl[2];
-    b.cl[1] = d.cl[3];
-    out.push_back(a);
-    out.push_back(b);
+    int rc = lower_clauses(g.in_type, g.clauses, g.nclauses, g.flags, cl);
+    if (rc != ACCR_OK) return rc;
+    ClauseMemo::Entry &x = m.e[m.next];
+    m.next = (m.next + 1) & 3;
+    x.valid = true;
+    x.in_type = g.in_type;
+    x.nc = g.nclauses;
+    x.flags = g.flags;
+    for (int c = 0; c < x.nc; ++c) {
+        x.op[c] = g.clauses[c].op;
+        x.acc[c] = g.clauses[c].acc_type;
+        x.init[c] = g.clauses[c].init;
+        x.dev[c] = cl[c];
+    }
+    return ACCR_OK;
+}
+
+// ---- host: plans -------------------------------------------------------------------
+
+constexpr int NKEY = 8 * 64;
+
+// Queue key: grouped by (element type, clause count) so that neighbouring work
+// runs the same code, largest first within a group so that the small pieces
+// fill in at the end.
+static int key_of(int in_type, int nc, int64_t bytes) {
+    return (in_type * 2 + (nc - 1)) * 64 + (63 - log2_floor((uint64_t)(bytes > 0 ? bytes : 1)));
+}
+
+// One contiguous range of source items (regions or segments) of a plan.
+struct PlanChunk {
+    int64_t s0 = 0, s1 = 0;  // source items
+    int64_t d0 = 0, nd = 0;  // its descriptors
+    int64_t slots = 0;       // partial slots (tiles) of its tiled descriptors
+    std::vector<int64_t> tpos, spos;  // per key: counts, then queue positions
+    int rc = ACCR_OK;
+    std::string msg;
+};
+
+// The caller's region descriptors.
+struct RegionSource {
+    const accr_region *regs;
+    int ndesc(int64_t i) const { return regs[i].nclauses > RD_CLAUSES ? 2 : 1; }
+    // Lowers item i into out[0..ndesc); returns ACCR_OK or an error code.
+    int fill(int64_t i, RegionDev *out, ClauseMemo &m) const {
+        const accr_region &g = regs[i];
+        if (g.flags & ~ACCR_COMPENSATED) return set_error(ACCR_EINVAL, "region %lld: bad flags", (long long)i);
+        ClauseDev cl[ACCR_MAX_CLAUSES];
+        int rc = lower_region(g, i, m, cl);
+        if (rc != ACCR_OK) return rc;
+        rc = check_region_ptr(g.in, g.n, g.in_type, i);
+        if (rc != ACCR_OK) return rc;
+        put(out, g.in, g.n, g.in_type, cl, g.nclauses);
+        return ACCR_OK;
+    }
+    // Descriptors over the same elements: clauses 0-1, then 2-3.
+    static void put(RegionDev *out, const void *in, int64_t n, int in_type, const ClauseDev *cl, int nc) {
+        for (int c0 = 0, j = 0; c0 < nc; c0 += RD_CLAUSES, ++j) {
+            RegionDev &d = out[j];
+            d.in = in;
+            d.n = n;
+            d.tile0 = 0;
+            d.in_type = in_type;
+            d.nc = (nc - c0) < RD_CLAUSES ? (nc - c0) : RD_CLAUSES;
+            d.cl[0] = cl[c0];
+            if (d.nc > 1) d.cl[1] = cl[c0 + 1];
+            else memset(&d.cl[1], 0, sizeof d.cl[1]);
+        }
+    }
+};
+
+// Segments [off[s], off[s+1]) of one array, one variable per segment.
+struct SegmentSource {
+    const void *values;
+    const int64_t *off;
+    int in_type, nc;
+    int64_t eb;
+    const ClauseDev *base;  // lowered clauses; out = the arrays' starts
+    int ndesc(int64_t) const { return nc > RD_CLAUSES ? 2 : 1; }
+    int fill(int64_t s, RegionDev *out, ClauseMemo &) const {
+        const int64_t lo = off[s], hi = off[s + 1];
+        if (lo < 0 || hi < lo)
+            return set_error(ACCR_EINVAL, "segmented: offsets not non-decreasing at %lld", (long long)s);
+        const void *in = (const char *)values + lo * eb;
+        int rc = check_region_ptr(in, hi - lo, in_type, s);
+        if (rc != ACCR_OK) return rc;
+        if (hi > lo && !values) return set_error(ACCR_EINVAL, "segmented: values is NULL");
+        ClauseDev cl[ACCR_MAX_CLAUSES];
+        for (int c = 0; c < nc; ++c) {
+            cl[c] = base[c];
+            cl[c].out = (char *)base[c].out + s * type_bytes(base[c].acc_type);
+        }
+        RegionSource::put(out, in, hi - lo, in_type, cl, nc);
+        return ACCR_OK;
+    }
+};
+
+// Builds the plan of n source items: each descriptor goes to the warp list
+// or to tiles by its own type and length, and both queues are ordered by key
+// (a counting sort).  Large plans run in chunks on the planner threads; the
+// queues come out in the same order as a serial pass would give (by key, then
+// descriptor, then tile).
+template <typename Src>
+static int plan_chunked(const Src &src, int64_t n, HostPlan &P) {
+    const int64_t small_b = g_small_bytes.load(), tile_b = P.tile_override > 0 ? P.tile_override : g_tile_bytes.load();
+    P.tile_bytes = tile_b;
+    const int nch = n >= PAR_MIN_REGIONS ? 2 * plan_pool().threads() : 1;
+    std::vector<PlanChunk> ch((size_t)nch);
+    for (int c = 0; c < nch; ++c) {
+        ch[c].s0 = n * c / nch;
+        ch[c].s1 = n * (c + 1) / nch;
+    }
+    // descriptors per chunk (a region with three or four clauses has two)
+    plan_for(n, nch, [&](int c) {
+        int64_t nd = 0;
+        for (int64_t i = ch[c].s0; i < ch[c].s1; ++i) nd += src.ndesc(i);
+        ch[c].nd = nd;
+    });
+    int64_t D = 0;
+    for (PlanChunk &k : ch) {
+        k.d0 = D;
+        D += k.nd;
+    }
+    if (D > INT32_MAX / 2) return set_error(ACCR_EINVAL, "batch: too many regions");
+    P.regions.resize((size_t)D);
+    // lower every item into its descriptors; count queue entries per key
+    plan_for(n, nch, [&](int c) {
+        PlanChunk &k = ch[c];
+        k.tpos.assign(NKEY, 0);
+        k.spos.assign(NKEY, 0);
+        k.slots = 0;
+        ClauseMemo memo;
+        int64_t d = k.d0;
+        for (int64_t i = k.s0; i < k.s1; ++i) {
+            const int nd = src.ndesc(i);
+            const int rc = src.fill(i, &P.regions[(size_t)d], memo);
+            if (rc != ACCR_OK) {
+                k.rc = rc;
+                k.msg = accr_last_error();
+                return;
+            }
+            for (int j = 0; j < nd; ++j, ++d) {
+                RegionDev &x = P.regions[(size_t)d];
+                const int64_t eb = type_bytes(x.in_type);
+                if (x.n * eb <= small_b) {
+                    x.tile0 = -1;
+                    k.spos[key_of(x.in_type, x.nc, x.n * eb)]++;
+                } else {
+                    const int64_t te = tile_b / eb, nt = (x.n + te - 1) / te;
+                    x.tile0 = k.slots;  // chunk-relative until the bases are known
+                    k.slots += nt;
+                    k.tpos[key_of(x.in_type, x.nc, tile_b)] += nt - 1;
+                    k.tpos[key_of(x.in_type, x.nc, (x.n - (nt - 1) * te) * eb)]++;
+                }
+            }
+        }
+    });
+    for (PlanChunk &k : ch)
+        if (k.rc != ACCR_OK) return set_error(k.rc, "%s", k.msg.c_str());
+    // tile bases per chunk; queue positions per (key, chunk)
+    std::vector<int64_t> base((size_t)nch);
+    int64_t slots = 0;
+    for (int c = 0; c < nch; ++c) {
+        base[c] = slots;
+        slots += ch[c].slots;
+    }
+    if (slots > INT32_MAX) return set_error(ACCR_EINVAL, "batch: more than 2^31 tiles");
+    int64_t tp = 0, sp = 0;
+    for (int key = 0; key < NKEY; ++key) {
+        for (PlanChunk &k : ch) {
+            const int64_t t = k.tpos[key], u = k.spos[key];
+            k.tpos[key] = tp;
+            k.spos[key] = sp;
+            tp += t;
+            sp += u;
+        }
+    }
+    P.ntiles = slots;
+    P.tiles.resize((size_t)tp);
+    P.small.resize((size_t)sp);
+    plan_for(n, nch, [&](int c) {
+        PlanChunk &k = ch[c];
+        for (int64_t d = k.d0; d < k.d0 + k.nd; ++d) {
+            RegionDev &x = P.regions[(size_t)d];
+            const int64_t eb = type_bytes(x.in_type);
+            if (x.tile0 < 0) {
+                P.small[(size_t)k.spos[key_of(x.in_type, x.nc, x.n * eb)]++] = (int32_t)d;
+                continue;
+            }
+            x.tile0 += base[c];
+            const int64_t te = tile_b / eb, nt = (x.n + te - 1) / te;
+            const int kfull = key_of(x.in_type, x.nc, tile_b);
+            const int klast = key_of(x.in_type, x.nc, (x.n - (nt - 1) * te) * eb);
+            for (int64_t t = 0; t < nt; ++t)
+                P.tiles[(size_t)k.tpos[t + 1 < nt ? kfull : klast]++] = make_int2((int)d, (int)t);
+        }
+    });
+    P.off_tiles = align_up(sizeof(RegionDev) * P.regions.size(), 256);
+    P.off_small = align_up(P.off_tiles + sizeof(int2) * P.tiles.size(), 256);
+    P.plan_bytes = P.off_small + 4 * P.small.size();
+    P.off_partials = align_up(P.plan_bytes, 256);
+    P.total_bytes = P.off_partials + sizeof(Partial) * RD_CLAUSES * (size_t)P.ntiles + 256;
+    return ACCR_OK;
+}
+
+// Copies the plan (descriptors, tile queue, warp queue) into dst, in pieces
+// on the planner threads when it is large.
+static void write_plan(const HostPlan &P, char *dst) {
+    struct Piece {
+        char *to;
+        const char *from;
+        size_t bytes;
+    };
+    const Piece parts[3] = {{dst, (const char *)P.regions.data(), sizeof(RegionDev) * P.regions.size()},
+                            {dst + P.off_tiles, (const char *)P.tiles.data(), sizeof(int2) * P.tiles.size()},
+                            {dst + P.off_small, (const char *)P.small.data(), 4 * P.small.size()}};
+    const int64_t R = (int64_t)P.regions.size();
+    const int pieces = R >= PAR_MIN_REGIONS ? 2 * plan_pool().threads() : 1;
+    plan_for(R, pieces, [&](int c) {
+        for (const Piece &q : parts) {
+            const size_t lo = q.bytes * (size_t)c / (size_t)pieces, hi = q.bytes * (size_t)(c + 1) / (size_t)pieces;
+            if (hi > lo) memcpy(q.to + lo, q.from + lo, hi - lo);
+        }
+    });
 }
 
 static int plan_from_regions(const accr_region *regs, int64_t R, HostPlan &P) {
     if (R < 0 || (R > 0 && !regs)) return set_error(ACCR_EINVAL, "batch: bad region array");
     if (R > INT32_MAX / 2) return set_error(ACCR_EINVAL, "batch: too many regions");
-    P.regions.clear();
-    P.regions.reserve((size_t)R);
-    for (int64_t r = 0; r < R; ++r) {
-        const accr_region &g = regs[r];
-        if (g.flags & ~ACCR_COMPENSATED) return set_error(ACCR_EINVAL, "region %lld: bad flags", (long long)r);
-        RegionDev d;
-        memset(&d, 0, sizeof d);
-        int rc = lower_clauses(g.in_type, g.clauses, g.nclauses, g.flags, d.cl);
-        if (rc != ACCR_OK) return rc;
-        rc = check_region_ptr(g.in, g.n, g.in_type, r);
-        if (rc != ACCR_OK) return rc;
-        d.in = g.in;
-        d.n = g.n;
-        d.in_type = g.in_type;
-        d.nc = g.nclauses;
-        push_split(P.regions, d);
-    }
-    return finish_plan(P);
+    RegionSource src{regs};
+    return plan_chunked(src, R, P);
 }
 
 static int plan_from_segments(const void *values, const int64_t *off, int64_t nseg, int in_type,
@@ -469,28 +742,8 @@ static int plan_from_segments(const void *values, const int64_t *off, int64_t ns
     ClauseDev base[ACCR_MAX_CLAUSES];
     int rc = lower_clauses(in_type, clauses, nc, flags & ACCR_COMPENSATED, base);
     if (rc != ACCR_OK) return rc;
-    const int64_t eb = type_bytes(in_type);
-    P.regions.clear();
-    P.regions.reserve((size_t)nseg * (nc > 2 ? 2 : 1));
-    for (int64_t s = 0; s < nseg; ++s) {
-        const int64_t lo = off[s], hi = off[s + 1];
-        if (lo < 0 || hi < lo) return set_error(ACCR_EINVAL, "segmented: offsets not non-decreasing at %lld", (long long)s);
-        RegionDev d;
-        memset(&d, 0, sizeof d);
-        d.in = (const char *)values + lo * eb;
-        rc = check_region_ptr(d.in, hi - lo, in_type, s);
-        if (rc != ACCR_OK) return rc;
-        if (hi > lo && !values) return set_error(ACCR_EINVAL, "segmented: values is NULL");
-        d.n = hi - lo;
-        d.in_type = in_type;
-        d.nc = nc;
-        for (int c = 0; c < nc; ++c) {
-            d.cl[c] = base[c];
-            d.cl[c].out = (char *)base[c].out + s * type_bytes(base[c].acc_type);
-        }
-        push_split(P.regions, d);
-    }
-    return finish_plan(P);
+    SegmentSource src{values, off, in_type, nc, (int64_t)type_bytes(in_type), base};
+    return plan_chunked(src, nseg, P);
 }
 
 static int batch_grid(const HostPlan &P) {
@@ -650,8 +903,7 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
 }
 
 int batch_launch_regions(const accr_region *regions, int64_t nregions, accr_stream_t stream, int64_t tile_bytes) {
-    HostPlan P;
-    P.tile_override = tile_bytes;
+    HostPlan &P = thread_plan(tile_bytes);
     int rc = plan_from_regions(regions, nregions, P);
     if (rc != ACCR_OK) return rc;
     return run_once(P, 0, stream);
@@ -701,7 +953,7 @@ extern "C" ACCR_API int accr_batch_reduce(const accr_region *regions, int64_t nr
     if (flags & ~(ACCR_SYNC | ACCR_PLAIN))
         return set_error(ACCR_EINVAL, "accr_batch_reduce: unsupported flags 0x%x", flags);
     if (flags & ACCR_PLAIN) return run_plain(regions, nregions, flags, stream);
-    HostPlan P;
+    HostPlan &P = thread_plan(0);
     int rc = plan_from_regions(regions, nregions, P);
     if (rc != ACCR_OK) return rc;
     return run_once(P, flags, stream);
@@ -713,7 +965,7 @@ extern "C" ACCR_API int accr_segmented_reduce(const void *values, const int64_t 
     clear_error();
     if (flags & ~(ACCR_SYNC | ACCR_COMPENSATED))
         return set_error(ACCR_EINVAL, "accr_segmented_reduce: unsupported flags 0x%x", flags);
-    HostPlan P;
+    HostPlan &P = thread_plan(0);
     int rc = plan_from_segments(values, offsets, nseg, in_type, clauses, nclauses, flags, P);
     if (rc != ACCR_OK) return rc;
     return run_once(P, flags, stream);
