@@ -813,6 +813,8 @@ static int run_once(HostPlan &P, unsigned flags, accr_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const size_t R = P.regions.size();
     if (R == 0) return ACCR_OK;
+    log_msg(2, "batch: %zu descriptors, %zu tiles of %lld bytes, %zu warp regions", R, P.tiles.size(),
+            (long long)P.tile_bytes, P.small.size());
     StreamBufs *B = bufs_for(stream);
     std::lock_guard<std::mutex> lk(B->mu);
     // device plan + partials
@@ -949,6 +951,7 @@ static int run_plain(const accr_region *regs, int64_t R, unsigned flags, accr_st
 
 extern "C" ACCR_API int accr_batch_reduce(const accr_region *regions, int64_t nregions, uint32_t flags,
                                           accr_stream_t stream) {
+    ACCR_TRACE("accr_batch_reduce");
     clear_error();
     if (flags & ~(ACCR_SYNC | ACCR_PLAIN))
         return set_error(ACCR_EINVAL, "accr_batch_reduce: unsupported flags 0x%x", flags);
@@ -962,6 +965,7 @@ extern "C" ACCR_API int accr_batch_reduce(const accr_region *regions, int64_t nr
 extern "C" ACCR_API int accr_segmented_reduce(const void *values, const int64_t *offsets, int64_t nseg,
                                               int32_t in_type, const accr_clause *clauses, int32_t nclauses,
                                               uint32_t flags, accr_stream_t stream) {
+    ACCR_TRACE("accr_segmented_reduce");
     clear_error();
     if (flags & ~(ACCR_SYNC | ACCR_COMPENSATED))
         return set_error(ACCR_EINVAL, "accr_segmented_reduce: unsupported flags 0x%x", flags);
@@ -973,6 +977,7 @@ extern "C" ACCR_API int accr_segmented_reduce(const void *values, const int64_t 
 
 extern "C" ACCR_API int accr_batch_create(const accr_region *regions, int64_t nregions, uint32_t flags,
                                           accr_batch **out) {
+    ACCR_TRACE("accr_batch_create");
     clear_error();
     if (!out) return set_error(ACCR_EINVAL, "accr_batch_create: batch is NULL");
     *out = nullptr;
@@ -1025,6 +1030,7 @@ extern "C" ACCR_API int accr_batch_create(const accr_region *regions, int64_t nr
 }
 
 extern "C" ACCR_API int accr_batch_launch(accr_batch *b, accr_stream_t stream) {
+    ACCR_TRACE("accr_batch_launch");
     clear_error();
     if (!b) return set_error(ACCR_EINVAL, "accr_batch_launch: batch is NULL");
     if (!b->exec) return ACCR_OK;  // empty batch
@@ -1038,6 +1044,7 @@ extern "C" ACCR_API int accr_batch_launch(accr_batch *b, accr_stream_t stream) {
 }
 
 extern "C" ACCR_API int accr_batch_destroy(accr_batch *b) {
+    ACCR_TRACE("accr_batch_destroy");
     clear_error();
     if (!b) return ACCR_OK;
     int rc = ACCR_OK;

@@ -18,6 +18,21 @@ int cuda_check(cudaError_t e, const char *where);
 int launched(const char *what, int kernels = 1);
 void clear_error();
 
+// ---- tracing and logging ----------------------------------------------------
+// Every entry point opens an NVTX range named after itself for the length of
+// the call (shown by Nsight Systems and `ncu --nvtx`; with no tool attached a
+// range costs one predictable branch).
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+};
+#define ACCR_TRACE(name) ::accr::TraceRange accr_trace_range_(name)
+// Log level from the environment variable ACCR_LOG, read once: 0 (default)
+// silent; 1 every error as it is recorded; 2 also each call's shape and the
+// path it takes (grid, split form, plan size).  Lines go to stderr.
+int log_level();
+void log_msg(int level, const char *fmt, ...);
+
 // ---- host-side fault injection (tests) --------------------------------------
 // True if an injected fault of `kind` (ACCR_FAULT_*) fires now (and uses it up).
 bool fault_take(int kind);

@@ -10,6 +10,7 @@ using namespace accr;
 
 extern "C" ACCR_API int accr_matmul_nest(const float *a, const float *b, float *c, int64_t len, int32_t mode,
                                          uint32_t flags, accr_stream_t stream) {
+    ACCR_TRACE("accr_matmul_nest");
     clear_error();
     if (len < 0) return set_error(ACCR_EINVAL, "accr_matmul_nest: len < 0");
     if (flags & ~(ACCR_SYNC | ACCR_MM_REUSE_SPLIT))
@@ -18,6 +19,8 @@ extern "C" ACCR_API int accr_matmul_nest(const float *a, const float *b, float *
     if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 3)
         return set_error(ACCR_EINVAL, "accr_matmul_nest: matrices must be 4-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
+    log_msg(2, "accr_matmul_nest: len=%lld mode=%d%s", (long long)len, mode,
+            (flags & ACCR_MM_REUSE_SPLIT) ? " (split reused if the operands are unchanged)" : "");
     int rc;
     switch (mode) {
     case ACCR_MM_SIMT: rc = matmul_simt(a, b, c, len, false, s); break;

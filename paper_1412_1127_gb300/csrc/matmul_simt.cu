@@ -229,6 +229,7 @@ int matmul_simt(const float *a, const float *b, float *c, int64_t len, bool seri
 }  // namespace accr
 
 extern "C" ACCR_API int accr_probe_fma(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream) {
+    ACCR_TRACE("accr_probe_fma");
     accr::clear_error();
     if (ctas < 1 || rounds < 1 || !sink) return accr::set_error(ACCR_EINVAL, "accr_probe_fma: bad arguments");
     int rc = accr::launch_guard("fma_probe_kernel");
@@ -238,6 +239,7 @@ extern "C" ACCR_API int accr_probe_fma(int32_t ctas, int64_t rounds, float *sink
 }
 
 extern "C" ACCR_API int accr_probe_fma_packed(int32_t ctas, int64_t rounds, float *sink, accr_stream_t stream) {
+    ACCR_TRACE("accr_probe_fma_packed");
     accr::clear_error();
     if (ctas < 1 || rounds < 1 || !sink) return accr::set_error(ACCR_EINVAL, "accr_probe_fma_packed: bad arguments");
     int rc = accr::launch_guard("fma2_probe_kernel");

@@ -567,6 +567,7 @@ int selftest_wait_timeout(uint32_t tries, cudaStream_t s) {
 }  // namespace accr
 
 extern "C" ACCR_API int accr_selftest_wait_timeout(uint32_t tries, accr_stream_t stream) {
+    ACCR_TRACE("accr_selftest_wait_timeout");
     accr::clear_error();
     return accr::selftest_wait_timeout(tries, (cudaStream_t)stream);
 }

@@ -906,6 +906,7 @@ using namespace accr;
 
 extern "C" ACCR_API int accr_nearest_k(const float *pts, int64_t n, float qx, float qy, int32_t k,
                                        int64_t *idx_out, float *d2_out, uint32_t flags, accr_stream_t stream) {
+    ACCR_TRACE("accr_nearest_k");
     clear_error();
     if (n < 0 || k < 1 || k > 16) return set_error(ACCR_EINVAL, "accr_nearest_k: need n >= 0 and 1 <= k <= 16");
     if (flags & ~ACCR_SYNC) return set_error(ACCR_EINVAL, "accr_nearest_k: unsupported flags 0x%x", flags);
@@ -930,6 +931,7 @@ static StdState g_std;
 
 extern "C" ACCR_API int accr_standardize(const float *x, int64_t n, float *y, double *stats, uint32_t flags,
                                          accr_stream_t stream) {
+    ACCR_TRACE("accr_standardize");
     clear_error();
     if (n < 0 || (n > 0 && (!x || !y)) || !stats) return set_error(ACCR_EINVAL, "accr_standardize: bad arguments");
     if (((uintptr_t)x & 3) || ((uintptr_t)y & 3) || ((uintptr_t)stats & 7))
@@ -1024,6 +1026,7 @@ extern "C" ACCR_API int accr_standardize(const float *x, int64_t n, float *y, do
 
 extern "C" ACCR_API int accr_grid_bfs(const uint8_t *open, int64_t rows, int64_t cols, int64_t src, int32_t *dist,
                                       int32_t mode, int64_t *levels, accr_stream_t stream) {
+    ACCR_TRACE("accr_grid_bfs");
     clear_error();
     if (rows < 0 || cols < 0 || (rows * cols > 0 && (!open || !dist)) || !levels)
         return set_error(ACCR_EINVAL, "accr_grid_bfs: bad arguments");

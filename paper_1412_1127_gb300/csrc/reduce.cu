@@ -317,6 +317,7 @@ using namespace accr;
 
 extern "C" ACCR_API int accr_reduce(const void *in, int64_t n, int32_t in_type, const accr_clause *clauses,
                            int32_t nclauses, uint32_t flags, accr_stream_t stream) {
+    ACCR_TRACE("accr_reduce");
     clear_error();
     if (flags & ~(ACCR_COMPENSATED | ACCR_SYNC | ACCR_TWO_LEVEL_HOST))
         return set_error(ACCR_EINVAL, "accr_reduce: unknown flags 0x%x", flags);
@@ -329,6 +330,8 @@ extern "C" ACCR_API int accr_reduce(const void *in, int64_t n, int32_t in_type, 
         return set_error(ACCR_EINVAL, "accr_reduce: in is not aligned to its element size");
     const int grid = reduce_grid(in_type, nclauses, n);
     const size_t pbytes = (size_t)nclauses * (size_t)grid * sizeof(Partial);
+    log_msg(2, "accr_reduce: n=%lld type=%d clauses=%d grid=%d%s", (long long)n, in_type, nclauses, grid,
+            (flags & ACCR_TWO_LEVEL_HOST) ? " (two-level host merge)" : "");
     Scratch *scr = scratch_for(stream, pbytes);
     if (!scr) return ACCR_ENOMEM;
     cudaStream_t s = (cudaStream_t)stream;

@@ -63,6 +63,7 @@ using namespace accr;
 extern "C" ACCR_API int accr_reduce_noalloc(const void *in, int64_t n, int32_t in_type,
                                             const accr_clause *clauses, int32_t nclauses, uint32_t flags,
                                             accr_stream_t stream) {
+    ACCR_TRACE("accr_reduce_noalloc");
     clear_error();
     if (flags & ~(ACCR_COMPENSATED | ACCR_SYNC))
         return set_error(ACCR_EINVAL, "accr_reduce_noalloc: unsupported flags 0x%x (only ACCR_COMPENSATED, "

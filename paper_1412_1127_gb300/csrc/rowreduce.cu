@@ -313,6 +313,7 @@ using namespace accr;
 extern "C" ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols, int64_t ld, int32_t in_type,
                               const accr_clause *clauses, int32_t nclauses, uint32_t flags,
                               accr_stream_t stream) {
+    ACCR_TRACE("accr_rowreduce");
     clear_error();
     if (flags & ~(ACCR_COMPENSATED | ACCR_SYNC))
         return set_error(ACCR_EINVAL, "accr_rowreduce: unsupported flags 0x%x", flags);
@@ -329,6 +330,8 @@ extern "C" ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols
     RowArgs a;
     memset(&a, 0, sizeof a);
     const int64_t eb = type_bytes(in_type), row_bytes = cols * eb;
+    log_msg(2, "accr_rowreduce: %lld x %lld (ld %lld) type=%d clauses=%d form=%s", (long long)rows, (long long)cols,
+            (long long)ld, in_type, nclauses, row_bytes >= SPLIT_ROW_BYTES ? "split rows" : "warp per row");
     if (row_bytes >= SPLIT_ROW_BYTES) {
         // chunked form: partials [rows][nclauses][cpr] and one counter per row
         a.chunk = SPLIT_CHUNK_BYTES / eb;

@@ -2,6 +2,7 @@
 // per-(device, stream) scratch cache of the accr library.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <string.h>
 #include <stdio.h>
 
@@ -11,12 +12,35 @@
 #include <string>
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace accr {
 
 static thread_local std::string t_last_error;
 static std::atomic<uint64_t> g_launches{0};
+
+int log_level() {
+    static const int level = [] {
+        const char *e = getenv("ACCR_LOG");
+        return e ? atoi(e) : 0;
+    }();
+    return level;
+}
+
+void log_msg(int level, const char *fmt, ...) {
+    if (log_level() < level) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "accr: %s\n", buf);
+}
+
+TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 
 int set_error(int code, const char *fmt, ...) {
     char buf[512];
@@ -25,6 +49,7 @@ int set_error(int code, const char *fmt, ...) {
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
     t_last_error = buf;
+    if (log_level() >= 1) fprintf(stderr, "accr: error %d: %s\n", code, buf);
     return code;
 }
 

@@ -140,6 +140,8 @@ int accr_server::launch(Slot &s, std::unique_lock<std::mutex> &lk) {
     }
     if (take.empty()) return 0;
     inflight += (uint64_t)bytes;
+    log_msg(2, "server: batch of %zu regions, %lld bytes, %llu bytes in flight, %zu waiting", take.size(),
+            (long long)bytes, (unsigned long long)inflight, pending.size());
     s.busy = true;
     s.bytes = bytes;
     s.reqs = std::move(take);
@@ -208,6 +210,7 @@ void accr_server::run() {
 
 extern "C" ACCR_API int accr_server_create(uint64_t budget, int32_t nstreams, int32_t max_batch,
                                            accr_server **out) {
+    ACCR_TRACE("accr_server_create");
     clear_error();
     if (!out) return set_error(ACCR_EINVAL, "accr_server_create: server is NULL");
     *out = nullptr;
@@ -234,6 +237,7 @@ extern "C" ACCR_API int accr_server_create(uint64_t budget, int32_t nstreams, in
 }
 
 extern "C" ACCR_API int accr_submit(accr_server *S, const accr_region *region, uint64_t *ticket) {
+    ACCR_TRACE("accr_submit");
     clear_error();
     if (!S || !region || !ticket) return set_error(ACCR_EINVAL, "accr_submit: NULL argument");
     int rc = check_region(*region);
@@ -269,6 +273,7 @@ extern "C" ACCR_API int accr_submit(accr_server *S, const accr_region *region, u
 }
 
 extern "C" ACCR_API int accr_poll(accr_server *S, uint64_t ticket, accr_result *out, int64_t timeout_us) {
+    ACCR_TRACE("accr_poll");
     clear_error();
     if (!S || !out) return set_error(ACCR_EINVAL, "accr_poll: NULL argument");
     std::unique_lock<std::mutex> lk(S->mu);
@@ -289,6 +294,7 @@ extern "C" ACCR_API int accr_poll(accr_server *S, uint64_t ticket, accr_result *
 }
 
 extern "C" ACCR_API int accr_server_destroy(accr_server *S) {
+    ACCR_TRACE("accr_server_destroy");
     clear_error();
     if (!S) return ACCR_OK;
     {
@@ -323,6 +329,7 @@ static void wait_until(int64_t t) {
 extern "C" ACCR_API int accr_server_replay(accr_server *S, const accr_region *regions, const double *arrival_s,
                                            int64_t n, uint32_t flags, accr_stream_t stream,
                                            accr_result *results) {
+    ACCR_TRACE("accr_server_replay");
     clear_error();
     if (n < 0 || (n > 0 && (!regions || !arrival_s || !results)))
         return set_error(ACCR_EINVAL, "accr_server_replay: bad arguments");

@@ -104,3 +104,27 @@ def test_submit_and_server_reject_bad_arguments_on_host(L):
     assert L.accr_batch_create(None, 0, 0, None) == _native.ACCR_EINVAL
     assert L.accr_batch_tiling(17, 0, None, None) == _native.ACCR_EINVAL
     assert L.accr_matmul_nest(None, None, None, 4, 9, 0, None) == _native.ACCR_EINVAL
+
+
+def _run_bad_call(env_level):
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1412_1127_gb300 import _native\n"
+            "print(_native.lib().accr_reduce(None, -1, 0, None, 1, 0, None))\n") % ROOT
+    env = dict(os.environ)
+    env.pop("ACCR_LOG", None)
+    if env_level is not None:
+        env["ACCR_LOG"] = str(env_level)
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+
+
+def test_log_level_reports_errors_on_stderr(L):
+    """ACCR_LOG=1 prints each recorded error to stderr; by default the library
+    is silent.  (The failing call is rejected on the host: no GPU needed.)"""
+    quiet = _run_bad_call(None)
+    loud = _run_bad_call(1)
+    assert quiet.returncode == 0 and loud.returncode == 0
+    assert quiet.stdout.strip() == loud.stdout.strip() == str(_native.ACCR_EINVAL)
+    assert "accr:" not in quiet.stderr
+    assert "accr: error %d: accr_reduce: n = -1 < 0" % _native.ACCR_EINVAL in loud.stderr
