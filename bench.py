@@ -253,6 +253,74 @@ def cpu_all_cores(host, regions, n):
     return {"value": round(sb / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "seconds": round(dt, 2)}
 
 
+def oracle_baselines():
+    """The serial oracle timed on this host beside each sub-measurement, on a
+    bounded sample of the same workload (one core; a baseline, not a target)."""
+    import oracle
+    from paper_1412_1127_gb300 import inputs
+
+    def timed(fn, warm=True):
+        if warm:
+            fn()  # library loaded, pages touched
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    out = {}
+    A = inputs.uniform_matrix(1024, 4096)
+    dt = timed(lambda: (oracle.rowreduce(A, "add"), oracle.rowreduce(A, "max")))
+    out["rows"] = {"value": round(A.nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": "1024 x 4096 float U(-1,1), row sum and row max (serial C, one fold each)",
+                   "seconds": round(dt, 3)}
+    lengths = inputs.log_uniform_lengths(20000, 1, 1 << 20)[:400]
+    xs = [inputs.normal(int(n), np.float32, salt=k) if k % 2 == 0 else
+          inputs.uniform_i64(int(n), -(1 << 40), 1 << 40, salt=k) for k, n in enumerate(lengths)]
+    nb = sum(x.nbytes for x in xs)
+
+    def batch():
+        for k, x in enumerate(xs):
+            if k % 2 == 0:
+                oracle.reduce(x, "add", "f32")
+            else:
+                oracle.reduce(x, "add", "i64")
+                oracle.reduce(x, "bxor", "i64")
+    dt = timed(batch)
+    out["batched"] = {"value": round(len(xs) / dt, 1), "unit": "regions/s", "gbs": round(nb / dt / 1e9, 4),
+                      "cores": 1, "kind": "oracle", "seconds": round(dt, 3),
+                      "sample": "the first 400 regions of the 20,000-region length mix (serial C per region)"}
+    sl = inputs.log_uniform_lengths(1000, 1 << 8, 1 << 26, seed=5, salt=4)
+    keep = int(np.searchsorted(np.cumsum(sl), 1 << 27))  # regions until 2^27 elements in all
+    sx = [inputs.full_range_i32(int(n), salt=k) for k, n in enumerate(sl[:max(keep, 1)])]
+
+    def served():
+        for x in sx:
+            oracle.reduce(x, "add", "i64")
+            oracle.reduce(x, "max", "i32")
+    dt = timed(served, warm=False)
+    out["served"] = {"value": round(len(sx) / dt, 1), "unit": "regions/s",
+                     "gbs": round(sum(x.nbytes for x in sx) / dt / 1e9, 4), "cores": 1, "kind": "oracle",
+                     "seconds": round(dt, 3),
+                     "sample": "%d regions of the served length mix (the first ones up to 2^27 elements; int32, "
+                               "+ into int64 and max), back to back" % len(sx)}
+    a, b = inputs.uniform_matrix(512, 512, salt=1), inputs.uniform_matrix(512, 512, salt=2)
+    dt = timed(lambda: oracle.matmul_listing1(a, b))
+    out["matmul"] = {"value": round(2 * 512 ** 3 / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                     "sample": "Listing 1a at LEN 512 (serial C, float accumulator)", "seconds": round(dt, 3)}
+    pts = (inputs.rng(21, 5).random((1 << 22, 2), dtype=np.float32) * 100).astype(np.float32)
+    x = inputs.normal(1 << 22, np.float32, salt=3)
+    g = inputs.rng(23, 1)
+    grid = (g.random((1024, 1024)) < 0.62).astype(np.uint8)
+    grid[512, 512] = 1
+    t_nk = timed(lambda: oracle.nearest_k(pts, 41.5, 58.25, 5))
+    t_sd = timed(lambda: oracle.standardize(x))
+    t_bfs = timed(lambda: oracle.grid_bfs(grid, 512 * 1024 + 512))
+    out["patterns"] = {"f4_nearest_k5_gbs": round(pts.nbytes / t_nk / 1e9, 4),
+                       "f2_standardize_gbs": round(3 * x.nbytes / t_sd / 1e9, 4),
+                       "f3_bfs_ms": round(t_bfs * 1e3, 2), "cores": 1, "kind": "oracle",
+                       "sample": "2^22 points (k = 5), 2^22 floats, the 1024 x 1024 grid (serial C)"}
+    return out
+
+
 def run_reference(args):
     """--impl reference: the serial oracle on the host cores, bounded sample."""
     rank, world, _ = dist_env()
@@ -421,6 +489,10 @@ def run_scalar(args):
         extra["patterns"] = measure_patterns(dev)
         torch.cuda.empty_cache()
         extra["one_region_2e20"] = measure_small_region(dev)
+        if not args.no_cpu_baseline:
+            base = oracle_baselines()
+            for k in ("rows", "batched", "served", "matmul", "patterns"):
+                extra[k]["cpu_baseline"] = base[k]
 
     if rank == 0:
         line = {
