@@ -1,4 +1,5 @@
-"""Autotuner of the batched-region split (warp-region threshold, tile size).
+"""Autotuner of the batched-region kernel: its split (warp-region threshold,
+tile size) and its vector widths (16-byte vectors in flight per thread).
 
 `tune(regions)` times every candidate (small_bytes, tile_bytes) pair on a
 representative batch with CUDA events and returns the fastest; `apply()`
@@ -7,11 +8,23 @@ function of each region's own type and length under a fixed pair, so once a
 pair is chosen every region keeps giving the same bits alone and in any batch;
 changing the pair changes the evaluation order of float sums.
 
-The chosen pair for GB300 is stored in ``tuning.json`` next to this file and
-applied by ``load()``.
+`tune_vectors()` builds the kernel with each candidate pair of vector widths
+(they are compile-time constants of the unrolled loops), times each build in a
+process of its own on the 20,000-region workload of both length mixes, and
+returns the fastest by the geometric mean; `save_vectors()` records it, and
+the build compiles the recorded widths in.  Changing the widths also changes
+the evaluation order of float sums.
+
+The chosen values for GB300 are stored in ``tuning.json`` next to this file:
+``load()`` applies the split, ``build.py`` reads the widths.
+
+    python -m paper_1412_1127_gb300.autotune --vectors [--save]
 """
 import json
+import math
 import os
+import subprocess
+import sys
 
 import torch
 
@@ -69,8 +82,102 @@ def load(path=TABLE):
 
 
 def save(small_bytes, tile_bytes, timings, path=TABLE, note=""):
-    d = {"small_bytes": int(small_bytes), "tile_bytes": int(tile_bytes), "note": note,
-         "timings_ms": {"%d,%d" % k: round(v, 4) for k, v in sorted(timings.items())}}
+    """Records the chosen split and its timings; other entries of the table
+    (the vector widths) are kept."""
+    d = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+    d.update({"small_bytes": int(small_bytes), "tile_bytes": int(tile_bytes), "note": note,
+              "timings_ms": {"%d,%d" % k: round(v, 4) for k, v in sorted(timings.items())}})
     with open(path, "w") as f:
         json.dump(d, f, indent=1)
     return d
+
+
+# (tile vectors per thread, warp-region vectors per lane, CTAs per SM the
+# registers are budgeted for)
+VECTOR_CANDIDATES = [(4, 8, 4), (4, 4, 4), (8, 8, 4), (2, 8, 4), (4, 16, 3), (8, 16, 3)]
+VECTOR_MIXES = (1 << 17, 1 << 20)
+
+
+def _workload(dev, hi, count=20000):
+    """The many-regions workload (lengths log-uniform on [1, hi]) on the device."""
+    from . import inputs
+    lengths, pf, off_f, pi, off_i = inputs.batched_regions(count, hi=hi)
+    tf, ti = torch.from_numpy(pf).to(dev), torch.from_numpy(pi).to(dev)
+    sf = torch.empty(len(off_f) - 1, dtype=torch.float32, device=dev)
+    si = torch.empty(len(off_i) - 1, dtype=torch.int64, device=dev)
+    xi = torch.empty(len(off_i) - 1, dtype=torch.int64, device=dev)
+    regions = []
+    for k in range(len(lengths)):
+        j = k // 2
+        if k % 2 == 0:
+            regions.append((tf[off_f[j]:off_f[j + 1]], [api.clause("add", sf[j:j + 1])], api.ACCR_COMPENSATED))
+        else:
+            regions.append((ti[off_i[j]:off_i[j + 1]], [api.clause("add", si[j:j + 1]),
+                                                        api.clause("bxor", xi[j:j + 1])], 0))
+    return regions, (tf, ti, sf, si, xi)
+
+
+def _time_this_library(mixes, reps):
+    """ms per prepared-batch launch of each length mix, with the split from
+    the table (runs in the process that loaded the candidate library)."""
+    load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    out = {}
+    for hi in mixes:
+        regions, keep = _workload(dev, hi)
+        d = load() or {"small_bytes": api.ACCR_SMALL_BYTES, "tile_bytes": api.ACCR_TILE_BYTES}
+        out[str(hi)] = min(time_batch(regions, d["small_bytes"], d["tile_bytes"], reps) for _ in range(2))
+        del regions, keep
+        torch.cuda.empty_cache()
+    return out
+
+
+def tune_vectors(candidates=VECTOR_CANDIDATES, mixes=VECTOR_MIXES, reps=10):
+    """Builds and times every candidate; returns (best, {candidate: {mix: ms}})."""
+    from . import build
+    res = {}
+    for cand in candidates:
+        bu, su, mb = cand
+        out_dir = os.path.join(build.BUILD, "vectors_%d_%d_%d" % cand)
+        lib = build.build_batch_variant(["-DACCR_BATCH_BU=%d" % bu, "-DACCR_BATCH_SU=%d" % su,
+                                         "-DACCR_BATCH_MINB=%d" % mb], out_dir)
+        code = ("import json, sys; sys.path.insert(0, %r)\n"
+                "from paper_1412_1127_gb300 import _native\n"
+                "_native.LIB_PATH = %r\n"
+                "from paper_1412_1127_gb300 import autotune\n"
+                "print(json.dumps(autotune._time_this_library(%r, %d)))\n") % (
+                    os.path.dirname(build.PKG), lib, list(mixes), reps)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("timing candidate %s failed:\n%s" % (cand, r.stderr[-2000:]))
+        res[cand] = {int(k): v for k, v in json.loads(r.stdout.strip().splitlines()[-1]).items()}
+    score = {c: math.exp(sum(math.log(v) for v in t.values()) / len(t)) for c, t in res.items()}
+    return min(score, key=score.get), res
+
+
+def save_vectors(best, timings, path=TABLE, note=""):
+    """Records the chosen widths (and every candidate's timings) in the table."""
+    with open(path) as f:
+        d = json.load(f)
+    d["vectors"] = {"tile_vectors": int(best[0]), "warp_vectors": int(best[1]), "min_ctas_per_sm": int(best[2]),
+                    "note": note,
+                    "timings_ms": {"%d,%d,%d" % c: {"2^%d" % (int(k).bit_length() - 1): round(v, 4)
+                                                   for k, v in sorted(t.items())}
+                                   for c, t in sorted(timings.items())}}
+    with open(path, "w") as f:
+        json.dump(d, f, indent=1)
+    return d
+
+
+if __name__ == "__main__":
+    if "--vectors" in sys.argv:
+        best, res = tune_vectors()
+        print(json.dumps({"best": best, "timings_ms": {"%d,%d,%d" % c: t for c, t in res.items()}}))
+        if "--save" in sys.argv:
+            save_vectors(best, res, note="GB300 (152 SMs); ms per prepared-batch launch of the 20,000-region "
+                                         "workload, both length mixes, split from this table; best by the "
+                                         "geometric mean")

@@ -31,6 +31,24 @@ def nvcc():
     return "nvcc"
 
 
+def tuned_defines(table=None):
+    """Compile-time definitions from the autotuner's table ("vectors" in
+    tuning.json): the batched-region kernel's vectors in flight."""
+    import json
+    path = table or os.path.join(PKG, "tuning.json")
+    try:
+        with open(path) as f:
+            v = json.load(f).get("vectors") or {}
+    except (OSError, ValueError):
+        v = {}
+    out = []
+    for key, name in [("tile_vectors", "ACCR_BATCH_BU"), ("warp_vectors", "ACCR_BATCH_SU"),
+                      ("min_ctas_per_sm", "ACCR_BATCH_MINB")]:
+        if key in v:
+            out.append("-D%s=%d" % (name, int(v[key])))
+    return out
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -46,16 +64,24 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, jobs=None):
-    """Compile and link libaccr.so if any source or header changed."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, jobs=None, defines=None, build_dir=None, lib=None):
+    """Compile and link libaccr.so if any source, header or the tuning table
+    changed.  `defines`, `build_dir` and `lib` override the tuned definitions
+    and the output paths (the autotuner builds its candidates that way)."""
+    build_dir, lib = build_dir or BUILD, lib or LIB
+    os.makedirs(build_dir, exist_ok=True)
     srcs, hdrs = _sources(), _headers()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, [s] + hdrs)]
+    table = os.path.join(PKG, "tuning.json")
+    defs = tuned_defines() if defines is None else list(defines)
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+
+    def deps(s):  # the tuned widths reach batch.cu only
+        return [s] + hdrs + ([table] if s.endswith("batch.cu") and os.path.exists(table) else [])
+    todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, deps(s))]
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc()] + NVCC_FLAGS + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc()] + NVCC_FLAGS + (defs if s.endswith("batch.cu") else []) + ["-c", s, "-o", o + ".tmp"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -69,14 +95,35 @@ def build(force=False, verbose=False, jobs=None):
             for msg in ex.map(compile_one, todo):
                 if msg and verbose:
                     print(msg)
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    if force or todo or _stale(lib, objs):
+        tmp = lib + ".%d.tmp" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl", "-lrt"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_batch_variant(defines, out_dir):
+    """A library whose batched-region kernel is built with `defines` (the
+    other objects are the main build's): the autotuner times such variants.
+    Returns the library's path."""
+    build()
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(CSRC, "batch.cu")
+    obj = os.path.join(out_dir, "batch.o")
+    lib = os.path.join(out_dir, "libaccr.so")
+    r = subprocess.run([nvcc()] + NVCC_FLAGS + list(defines) + ["-c", src, "-o", obj], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for a batch variant:\n%s%s" % (r.stdout, r.stderr))
+    objs = [o for o in (os.path.join(BUILD, os.path.basename(x)[:-3] + ".o") for x in _sources())
+            if not o.endswith(os.sep + "batch.o")]
+    r = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", lib, obj] + objs + ["-lpthread", "-ldl", "-lrt"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed for a batch variant:\n%s%s" % (r.stdout, r.stderr))
+    return lib
 
 
 if __name__ == "__main__":

@@ -42,9 +42,22 @@ int reduce_grid(int in_type, int nc, int64_t n);
 int reduce_launch(const void *in, int64_t n, int in_type, const ClauseDev *cl, int nc, int two_level,
                   Partial *partials, unsigned *counter, int grid, cudaStream_t s);
 
-constexpr int BB = 256;  // threads per CTA (4 CTAs per SM: one CTA's merge between tiles overlaps the others' streaming)
-constexpr int BU = 4;    // 16-byte vectors per thread per iteration (tiles)
-constexpr int SU = 8;    // 16-byte vectors per lane per iteration (warp regions)
+// Vectors in flight: picked by the autotuner (paper_1412_1127_gb300/autotune.py,
+// "vectors" in tuning.json), which builds and times the candidates; the build
+// passes the chosen widths in.
+#ifndef ACCR_BATCH_BU
+#define ACCR_BATCH_BU 4
+#endif
+#ifndef ACCR_BATCH_SU
+#define ACCR_BATCH_SU 8
+#endif
+#ifndef ACCR_BATCH_MINB
+#define ACCR_BATCH_MINB 4
+#endif
+constexpr int BB = 256;              // threads per CTA (4 CTAs per SM: one CTA's merge between tiles overlaps the others' streaming)
+constexpr int BU = ACCR_BATCH_BU;    // 16-byte vectors per thread per iteration (tiles)
+constexpr int SU = ACCR_BATCH_SU;    // 16-byte vectors per lane per iteration (warp regions)
+constexpr int MINB = ACCR_BATCH_MINB;  // CTAs per SM the register budget is set for
 
 // A region's descriptor carries at most two clauses: a region with three or
 // four is planned as two descriptors over the same elements.
@@ -311,7 +324,7 @@ __device__ __forceinline__ void batch_body(const BatchArgs &p, const RegionDev *
     }
 }
 
-__global__ void __launch_bounds__(BB, 4) batch_kernel(const __grid_constant__ BatchArgs p) {
+__global__ void __launch_bounds__(BB, MINB) batch_kernel(const __grid_constant__ BatchArgs p) {
     batch_body(p, p.regions, p.tiles, p.small);
 }
 
@@ -327,7 +340,7 @@ struct BatchArgsInline {
 };
 static_assert(sizeof(BatchArgsInline) < 32000, "kernel parameters are limited to 32764 bytes");
 
-__global__ void __launch_bounds__(BB, 4) batch_kernel_inline(const __grid_constant__ BatchArgsInline p) {
+__global__ void __launch_bounds__(BB, MINB) batch_kernel_inline(const __grid_constant__ BatchArgsInline p) {
     batch_body(p.b, p.regions, p.tiles, p.small);
 }
 

@@ -61,3 +61,22 @@ def test_committed_tuning_table_is_consistent():
     d = json.load(open(autotune.TABLE))
     assert d["small_bytes"] % 16 == 0 and d["tile_bytes"] % 16 == 0 and d["tile_bytes"] >= 4096
     assert "%d,%d" % (d["small_bytes"], d["tile_bytes"]) in d["timings_ms"]
+
+
+def test_vector_widths_reach_the_build(tmp_path):
+    """The widths the vector autotuner records become compile-time definitions
+    of the batched-region kernel; the split tuner's save keeps them."""
+    from paper_1412_1127_gb300 import build
+    table = tmp_path / "tuning.json"
+    with open(autotune.TABLE) as f:
+        d = json.load(f)
+    d.pop("vectors", None)
+    table.write_text(json.dumps(d))
+    assert build.tuned_defines(str(table)) == []
+    timings = {(4, 8, 4): {1 << 17: 0.25, 1 << 20: 1.35}, (8, 16, 3): {1 << 17: 0.29, 1 << 20: 1.38}}
+    autotune.save_vectors((4, 8, 4), timings, path=str(table))
+    assert build.tuned_defines(str(table)) == ["-DACCR_BATCH_BU=4", "-DACCR_BATCH_SU=8", "-DACCR_BATCH_MINB=4"]
+    autotune.save(65536, 2097152, {(65536, 2097152): 1.33}, path=str(table))
+    got = json.loads(table.read_text())
+    assert got["vectors"]["tile_vectors"] == 4 and got["vectors"]["timings_ms"]["8,16,3"]["2^20"] == 1.38
+    assert got["small_bytes"] == 65536
