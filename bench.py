@@ -449,7 +449,7 @@ def run_scalar(args):
             stream.synchronize()
 
         e2e_step()
-        ek = max(2, min(args.steps, 5))
+        ek = max(10, min(args.steps, 20))  # at least 10 end-to-end steps (each copies 4 GiB in)
         t0 = time.perf_counter()
         for _ in range(ek):
             e2e_step()
