@@ -116,6 +116,22 @@ __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ R
 
     cta_merge<NC, RB>(w, ident, E64, A, sh);
     const int G = gridDim.x;
+    if (G == 1 && !p.two_level) {
+        // one CTA: its merge is the region's (the same operations the last-CTA
+        // merge below applies to a single partial: the final code's identity,
+        // then the partial)
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                Acc F;
+                F.a = final_ident(p.cl[c]);
+                F.c = 0.f;
+                merge(final_code(w[c]), E64, F, to_final(w[c], A[c]));
+                store_var(p.cl[c], 0, finish(p.cl[c], E64, n == 0, F));
+            }
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -128,15 +144,18 @@ __global__ void __launch_bounds__(RB, 2) reduce_kernel(const __grid_constant__ R
     }
     if (p.two_level) return;
 
-    // single-pass cross-gang merge: the last CTA to arrive merges all partials
+    // single-pass cross-gang merge: the last CTA to arrive merges all partials.
+    // The count is an acquire-release atomic at device scope: it publishes this
+    // CTA's partials (release) and, for the last CTA, makes every other CTA's
+    // partials visible to its thread 0 (acquire), and through the barrier to
+    // the whole CTA -- no separate fences.
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(p.counter, 1u);
+        unsigned t;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(t) : "l"(p.counter) : "memory");
         am_last = (t == (unsigned)G - 1u);
     }
     __syncthreads();
     if (!am_last) return;
-    __threadfence();
 
     int fw[NC];
     uint64_t fid[NC];

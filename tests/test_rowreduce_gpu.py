@@ -68,10 +68,12 @@ def test_two_clauses_rows_full_size():
     api.accr_rowreduce(At, [api.clause("add", gs.t), api.clause("max", gm.t)])
     m_np, s_np = gm.check("row max").cpu().numpy(), gs.check("row sum").cpu().numpy()
     assert same_bits(m_np, oracle.rowreduce(A, "max"))
-    idx = np.random.default_rng(0).choice(65536, size=64, replace=False)
-    for r in idx:
-        truth = oracle.truth_sum(A[r])
-        assert abs(float(s_np[r]) - truth) / max(abs(truth), 0.1 * 64 * 0.577) <= TOL_F32
+    # every row's sum against its exact sum (host threads; ctypes releases the GIL)
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        truths = np.array(list(ex.map(lambda r: oracle.truth_sum(A[r]), range(65536))))
+    err = np.abs(s_np.astype(np.float64) - truths) / np.maximum(np.abs(truths), 0.1 * 64 * 0.577)
+    assert float(err.max()) <= TOL_F32, (int(err.argmax()), float(err.max()))
 
 
 PAIR_CASES = [  # (element type, sum variable, flags) for the fixed-code two-clause kernels
