@@ -1109,7 +1109,8 @@ def run_batched(args):
     import torch
     import __graft_entry__
     torch.cuda.set_device(0)
-    r = measure_batched(torch.device("cuda", 0), args.steps, args.warmup, args.regions, args.tune)
+    r = measure_batched(torch.device("cuda", 0), args.steps, args.warmup, args.regions, args.tune,
+                        hi=args.batched_hi)
     print(json.dumps(r), flush=True)
     return 0
 
@@ -1131,6 +1132,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--regions", type=int, default=20000, help="regions of the batched workload")
+    ap.add_argument("--batched-hi", type=int, default=1 << 20,
+                    help="batched workload: largest region length (2^20, or 2^17 for the second mix)")
     ap.add_argument("--tune", action="store_true", help="batched: autotune the split first")
     ap.add_argument("--sweep", action="store_true", help="served: sweep the offered rate to saturation")
     ap.add_argument("--n", type=int, default=N_SCALAR,
