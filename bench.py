@@ -989,6 +989,22 @@ def run_rows(args):
     return 0
 
 
+def device_ms(fn, stream, reps):
+    """Device time per call of fn, calls back to back on `stream` (CUDA
+    events around all of them; the host queues ahead of the GPU)."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def measure_patterns(dev, reps=10, which=("f1", "f2", "f3", "f4")):
     """The paper's two-level host merge against the single-pass merge (f1),
     the SRAD pattern fused and unfused (f2), the BFS convergence flag in its
@@ -1039,6 +1055,10 @@ def measure_patterns(dev, reps=10, which=("f1", "f2", "f3", "f4")):
         for form, fl in [("fused", 0), ("unfused", api.ACCR_UNFUSED), ("two_level_host", api.ACCR_TWO_LEVEL_HOST)]:
             ms = wall(lambda: (api.accr_standardize(x, y, st, flags=fl, stream=stream), stream.synchronize()), reps)
             r[form] = {"ms": round(ms, 4), "gbs_3_passes": round(12.0 * n / (ms * 1e-3) / 1e9, 1)}
+            if form != "two_level_host":  # (the host form waits for the host inside the call)
+                dev_ms = device_ms(lambda: api.accr_standardize(x, y, st, flags=fl, stream=stream), stream, reps)
+                r[form]["device_ms"] = round(dev_ms, 4)
+                r[form]["device_gbs_3_passes"] = round(12.0 * n / (dev_ms * 1e-3) / 1e9, 1)
         f2["n=2^%d" % lg] = r
         del x, y
     if f2:

@@ -673,8 +673,8 @@ __device__ __forceinline__ void publish_stats(const StdArgs &p, const StatPartia
 
 // SU vectors in flight per thread; a group's loads all come before its
 // stores (each element is read and written by the same thread, so the order
-// is right even when y aliases x).  The separate elementwise launch gains from
-// four; inside the fused launch one is faster.
+// is right even when y aliases x).  Both the separate elementwise launch and
+// the fused launch's second pass keep four.
 template <int SU>
 __device__ __forceinline__ void map_pass(const float *x, float *y, int64_t n, float mean_f, float rstd_f) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(SD_THREADS) standardize_kernel(const __grid_co
                 atomicExch(p.err, 6);
                 break;
             }
-            __nanosleep(64);
+            if (i > 256) __nanosleep(64);  // the statistics usually arrive within a few hundred polls
         }
         s_ok = ok;
     }
@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(SD_THREADS) standardize_kernel(const __grid_co
     __threadfence();
     const float mean_f = *(volatile float *)&p.shared->mean_f;
     const float rstd_f = *(volatile float *)&p.shared->rstd_f;
-    map_pass<1>(p.x, p.y, p.n, mean_f, rstd_f);
+    map_pass<4>(p.x, p.y, p.n, mean_f, rstd_f);
 }
 
 __global__ void map_kernel(const float *x, float *y, int64_t n, const StdShared *st, float mean_f, float rstd_f,
