@@ -25,6 +25,12 @@
  *  - Element arrays must be aligned to their element size.  Any further
  *    alignment is handled inside (unaligned heads and ragged tails included).
  *  - Indices and lengths are 64-bit.
+ *  - Tracing and logging: every compute and serving entry point opens an NVTX
+ *    range named after itself for the length of the call (visible in Nsight
+ *    Systems and `ncu --nvtx`).  The environment variable ACCR_LOG, read once
+ *    per process, sets a log level on stderr: 0 or unset, silent; 1, every
+ *    error as it is recorded; 2, also each call's shape and the path it takes
+ *    (grid, row form, plan size, served batch).
  */
 #ifndef ACCR_H
 #define ACCR_H
