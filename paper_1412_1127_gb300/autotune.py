@@ -1,5 +1,6 @@
-"""Autotuner of the batched-region kernel: its split (warp-region threshold,
-tile size) and its vector widths (16-byte vectors in flight per thread).
+"""Autotuner of the streaming kernels: the batched-region split (warp-region
+threshold, tile size) and the vector widths (16-byte vectors in flight per
+thread) of the batched-region, single-region and row kernels.
 
 `tune(regions)` times every candidate (small_bytes, tile_bytes) pair on a
 representative batch with CUDA events and returns the fastest; `apply()`
@@ -8,17 +9,18 @@ function of each region's own type and length under a fixed pair, so once a
 pair is chosen every region keeps giving the same bits alone and in any batch;
 changing the pair changes the evaluation order of float sums.
 
-`tune_vectors()` builds the kernel with each candidate pair of vector widths
-(they are compile-time constants of the unrolled loops), times each build in a
-process of its own on the 20,000-region workload of both length mixes, and
-returns the fastest by the geometric mean; `save_vectors()` records it, and
-the build compiles the recorded widths in.  Changing the widths also changes
-the evaluation order of float sums.
+`tune_widths(kind)` builds a kernel with each candidate vector width (they
+are compile-time constants of the unrolled loops) -- the batched-region
+kernel (tile and warp-region widths), the single-region kernel, the row
+kernel -- times each build in a process of its own on that kernel's
+workloads, and returns the fastest by the geometric mean; `save_widths()`
+records it, and the build compiles the recorded widths in.  Changing a width
+also changes the evaluation order of float sums.
 
 The chosen values for GB300 are stored in ``tuning.json`` next to this file:
 ``load()`` applies the split, ``build.py`` reads the widths.
 
-    python -m paper_1412_1127_gb300.autotune --vectors [--save]
+    python -m paper_1412_1127_gb300.autotune [--batch] [--reduce] [--rows] [--all] [--save]
 """
 import json
 import math
@@ -95,9 +97,17 @@ def save(small_bytes, tile_bytes, timings, path=TABLE, note=""):
     return d
 
 
-# (tile vectors per thread, warp-region vectors per lane, CTAs per SM the
-# registers are budgeted for)
-VECTOR_CANDIDATES = [(4, 8, 4), (4, 4, 4), (8, 8, 4), (2, 8, 4), (4, 16, 3), (8, 16, 3)]
+# Vector-width candidates per kernel: (source file, its macros, candidates).
+# batch: (tile vectors per thread, warp-region vectors per lane, CTAs per SM
+# the registers are budgeted for); reduce: vectors per thread; rows: vectors
+# per lane.
+WIDTHS = {
+    "batch": ("batch.cu", ("ACCR_BATCH_BU", "ACCR_BATCH_SU", "ACCR_BATCH_MINB"),
+              [(4, 8, 4), (4, 4, 4), (8, 8, 4), (2, 8, 4), (4, 16, 3), (8, 16, 3)]),
+    "reduce": ("reduce.cu", ("ACCR_REDUCE_RU",), [(2,), (4,), (8,)]),
+    "rows": ("rowreduce.cu", ("ACCR_ROW_RU",), [(4,), (8,), (16,)]),
+}
+VECTOR_CANDIDATES = WIDTHS["batch"][2]
 VECTOR_MIXES = (1 << 17, 1 << 20)
 
 
@@ -120,64 +130,132 @@ def _workload(dev, hi, count=20000):
     return regions, (tf, ti, sf, si, xi)
 
 
-def _time_this_library(mixes, reps):
-    """ms per prepared-batch launch of each length mix, with the split from
-    the table (runs in the process that loaded the candidate library)."""
+def _events_ms(fn, reps):
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _time_this_library(kind, reps):
+    """{workload: ms} of the kernel `kind` in the library this process loaded
+    (the candidate's): batch -- a prepared batch of each length mix with the
+    table's split; reduce -- one region of 2^27 int32 (+ into int64), float
+    (compensated +) and double (+); rows -- row sum + row max of 65536 x 4096
+    and 64 x 2^22 floats."""
+    from . import inputs
     load()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     out = {}
-    for hi in mixes:
-        regions, keep = _workload(dev, hi)
-        d = load() or {"small_bytes": api.ACCR_SMALL_BYTES, "tile_bytes": api.ACCR_TILE_BYTES}
-        out[str(hi)] = min(time_batch(regions, d["small_bytes"], d["tile_bytes"], reps) for _ in range(2))
-        del regions, keep
-        torch.cuda.empty_cache()
+    if kind == "batch":
+        for hi in VECTOR_MIXES:
+            regions, keep = _workload(dev, hi)
+            d = load() or {"small_bytes": api.ACCR_SMALL_BYTES, "tile_bytes": api.ACCR_TILE_BYTES}
+            out[str(hi)] = min(time_batch(regions, d["small_bytes"], d["tile_bytes"], reps) for _ in range(2))
+            del regions, keep
+            torch.cuda.empty_cache()
+    elif kind == "reduce":
+        n = 1 << 27
+        cases = [("i32", torch.from_numpy(inputs.full_range_i32(n)).to(dev), torch.int64, 0),
+                 ("f32", torch.from_numpy(inputs.normal(n)).to(dev), torch.float32, api.ACCR_COMPENSATED),
+                 ("f64", torch.from_numpy(inputs.normal(n, dtype="float64")).to(dev), torch.float64, 0)]
+        for name, x, acc, fl in cases:
+            o = torch.empty(1, dtype=acc, device=dev)
+            cl = [api.clause("add", o)]
+            out[name] = _events_ms(lambda: api.accr_reduce(x, cl, flags=fl), reps)
+    else:
+        for rows, cols in [(65536, 4096), (64, 1 << 22)]:
+            A = torch.from_numpy(inputs.uniform_matrix(rows, cols)).to(dev)
+            s_ = torch.empty(rows, device=dev)
+            m_ = torch.empty(rows, device=dev)
+            cl = [api.clause("add", s_), api.clause("max", m_)]
+            out["%dx%d" % (rows, cols)] = _events_ms(lambda: api.accr_rowreduce(A, cl), reps)
+            del A
+            torch.cuda.empty_cache()
     return out
 
 
-def tune_vectors(candidates=VECTOR_CANDIDATES, mixes=VECTOR_MIXES, reps=10):
-    """Builds and times every candidate; returns (best, {candidate: {mix: ms}})."""
+def tune_widths(kind="batch", candidates=None, reps=10):
+    """Builds the kernel `kind` with every candidate width, times each build in
+    a process of its own, and returns (best, {candidate: {workload: ms}}): the
+    best by the geometric mean over the workloads."""
     from . import build
+    source, macros, default = WIDTHS[kind]
     res = {}
-    for cand in candidates:
-        bu, su, mb = cand
-        out_dir = os.path.join(build.BUILD, "vectors_%d_%d_%d" % cand)
-        lib = build.build_batch_variant(["-DACCR_BATCH_BU=%d" % bu, "-DACCR_BATCH_SU=%d" % su,
-                                         "-DACCR_BATCH_MINB=%d" % mb], out_dir)
+    for cand in candidates or default:
+        out_dir = os.path.join(build.BUILD, "widths_%s_%s" % (kind, "_".join(map(str, cand))))
+        lib = build.build_variant(source, ["-D%s=%d" % (m, v) for m, v in zip(macros, cand)], out_dir)
         code = ("import json, sys; sys.path.insert(0, %r)\n"
                 "from paper_1412_1127_gb300 import _native\n"
                 "_native.LIB_PATH = %r\n"
                 "from paper_1412_1127_gb300 import autotune\n"
                 "print(json.dumps(autotune._time_this_library(%r, %d)))\n") % (
-                    os.path.dirname(build.PKG), lib, list(mixes), reps)
+                    os.path.dirname(build.PKG), lib, kind, reps)
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError("timing candidate %s failed:\n%s" % (cand, r.stderr[-2000:]))
-        res[cand] = {int(k): v for k, v in json.loads(r.stdout.strip().splitlines()[-1]).items()}
+            raise RuntimeError("timing candidate %s of %s failed:\n%s" % (cand, kind, r.stderr[-2000:]))
+        res[tuple(cand)] = json.loads(r.stdout.strip().splitlines()[-1])
     score = {c: math.exp(sum(math.log(v) for v in t.values()) / len(t)) for c, t in res.items()}
     return min(score, key=score.get), res
 
 
-def save_vectors(best, timings, path=TABLE, note=""):
-    """Records the chosen widths (and every candidate's timings) in the table."""
+def tune_vectors(candidates=VECTOR_CANDIDATES, reps=10):
+    """The batched-region kernel's widths (see tune_widths)."""
+    best, res = tune_widths("batch", candidates, reps)
+    return best, {c: {int(k): v for k, v in t.items()} for c, t in res.items()}
+
+
+# table keys of each kind's widths, and of its timings
+_KEYS = {"batch": (("tile_vectors", "warp_vectors", "min_ctas_per_sm"), "timings_ms"),
+         "reduce": (("reduce_vectors",), "reduce_timings_ms"),
+         "rows": (("row_vectors",), "row_timings_ms")}
+
+
+def save_widths(kind, best, timings, path=TABLE, note=None):
+    """Records a kind's chosen widths (and every candidate's timings) in the
+    table's "vectors" entry, keeping the rest of the table."""
     with open(path) as f:
         d = json.load(f)
-    d["vectors"] = {"tile_vectors": int(best[0]), "warp_vectors": int(best[1]), "min_ctas_per_sm": int(best[2]),
-                    "note": note,
-                    "timings_ms": {"%d,%d,%d" % c: {"2^%d" % (int(k).bit_length() - 1): round(v, 4)
-                                                   for k, v in sorted(t.items())}
-                                   for c, t in sorted(timings.items())}}
+    v = d.get("vectors") or {}
+    keys, tkey = _KEYS[kind]
+    for k, b in zip(keys, best):
+        v[k] = int(b)
+    v[tkey] = {",".join(map(str, c)): {w: round(ms, 4) for w, ms in sorted(t.items())}
+               for c, t in sorted(timings.items())}
+    if note is not None:
+        v["note"] = note
+    d["vectors"] = v
     with open(path, "w") as f:
         json.dump(d, f, indent=1)
     return d
 
 
+def save_vectors(best, timings, path=TABLE, note=""):
+    """Records the batched-region kernel's widths (see save_widths)."""
+    t = {c: {"2^%d" % (int(k).bit_length() - 1): ms for k, ms in tt.items()} for c, tt in timings.items()}
+    return save_widths("batch", best, t, path, note)
+
+
+NOTE = ("GB300 (152 SMs); batch: ms per prepared-batch launch of the 20,000-region workload, both length mixes, "
+        "split from this table; reduce: ms per region of 2^27 int32 (+ into int64), float (compensated +), double "
+        "(+); rows: ms per row nest (sum + max) of 65536 x 4096 and 64 x 2^22 floats; each kind's best by the "
+        "geometric mean over its workloads")
+
+
 if __name__ == "__main__":
+    kinds = [k for k in ("batch", "reduce", "rows") if "--" + k in sys.argv or "--all" in sys.argv]
     if "--vectors" in sys.argv:
-        best, res = tune_vectors()
-        print(json.dumps({"best": best, "timings_ms": {"%d,%d,%d" % c: t for c, t in res.items()}}))
+        kinds.append("batch")
+    for kind in kinds:
+        best, res = tune_widths(kind)
+        print(json.dumps({"kind": kind, "best": best, "timings_ms": {",".join(map(str, c)): t for c, t in res.items()}}))
         if "--save" in sys.argv:
-            save_vectors(best, res, note="GB300 (152 SMs); ms per prepared-batch launch of the 20,000-region "
-                                         "workload, both length mixes, split from this table; best by the "
-                                         "geometric mean")
+            save_widths(kind, best, res, note=NOTE)

@@ -31,9 +31,17 @@ def nvcc():
     return "nvcc"
 
 
-def tuned_defines(table=None):
-    """Compile-time definitions from the autotuner's table ("vectors" in
-    tuning.json): the batched-region kernel's vectors in flight."""
+# Autotuned compile-time constants: (key in the table's "vectors", macro, source)
+TUNED = [("tile_vectors", "ACCR_BATCH_BU", "batch.cu"), ("warp_vectors", "ACCR_BATCH_SU", "batch.cu"),
+         ("min_ctas_per_sm", "ACCR_BATCH_MINB", "batch.cu"), ("reduce_vectors", "ACCR_REDUCE_RU", "reduce.cu"),
+         ("row_vectors", "ACCR_ROW_RU", "rowreduce.cu")]
+TUNED_SOURCES = sorted({src for _, _, src in TUNED})
+
+
+def tuned_defines(table=None, source="batch.cu"):
+    """Compile-time definitions of one source from the autotuner's table
+    ("vectors" in tuning.json): the vectors in flight of the batched-region,
+    single-region and row kernels."""
     import json
     path = table or os.path.join(PKG, "tuning.json")
     try:
@@ -41,12 +49,7 @@ def tuned_defines(table=None):
             v = json.load(f).get("vectors") or {}
     except (OSError, ValueError):
         v = {}
-    out = []
-    for key, name in [("tile_vectors", "ACCR_BATCH_BU"), ("warp_vectors", "ACCR_BATCH_SU"),
-                      ("min_ctas_per_sm", "ACCR_BATCH_MINB")]:
-        if key in v:
-            out.append("-D%s=%d" % (name, int(v[key])))
-    return out
+    return ["-D%s=%d" % (macro, int(v[key])) for key, macro, src in TUNED if src == source and key in v]
 
 
 def _sources():
@@ -66,22 +69,28 @@ def _stale(target, deps):
 
 def build(force=False, verbose=False, jobs=None, defines=None, build_dir=None, lib=None):
     """Compile and link libaccr.so if any source, header or the tuning table
-    changed.  `defines`, `build_dir` and `lib` override the tuned definitions
-    and the output paths (the autotuner builds its candidates that way)."""
+    changed.  `defines` ({source name: [flags]}), `build_dir` and `lib`
+    override the tuned definitions and the output paths."""
     build_dir, lib = build_dir or BUILD, lib or LIB
     os.makedirs(build_dir, exist_ok=True)
     srcs, hdrs = _sources(), _headers()
     table = os.path.join(PKG, "tuning.json")
-    defs = tuned_defines() if defines is None else list(defines)
     objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
-    def deps(s):  # the tuned widths reach batch.cu only
-        return [s] + hdrs + ([table] if s.endswith("batch.cu") and os.path.exists(table) else [])
+    def defs_for(s):
+        name = os.path.basename(s)
+        if defines is not None:
+            return list(defines.get(name, [])) if isinstance(defines, dict) else []
+        return tuned_defines(source=name)
+
+    def deps(s):  # the tuned widths reach their own sources only
+        tuned = os.path.basename(s) in TUNED_SOURCES and os.path.exists(table)
+        return [s] + hdrs + ([table] if tuned else [])
     todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, deps(s))]
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc()] + NVCC_FLAGS + (defs if s.endswith("batch.cu") else []) + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc()] + NVCC_FLAGS + defs_for(s) + ["-c", s, "-o", o + ".tmp"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -105,25 +114,29 @@ def build(force=False, verbose=False, jobs=None, defines=None, build_dir=None, l
     return lib
 
 
-def build_batch_variant(defines, out_dir):
-    """A library whose batched-region kernel is built with `defines` (the
-    other objects are the main build's): the autotuner times such variants.
-    Returns the library's path."""
+def build_variant(source, defines, out_dir):
+    """A library whose `source` (a csrc file name, e.g. "batch.cu") is built
+    with `defines` instead of the tuned ones; the other objects are the main
+    build's.  The autotuner times such variants.  Returns the library's path."""
     build()
     os.makedirs(out_dir, exist_ok=True)
-    src = os.path.join(CSRC, "batch.cu")
-    obj = os.path.join(out_dir, "batch.o")
+    src = os.path.join(CSRC, source)
+    obj = os.path.join(out_dir, source[:-3] + ".o")
     lib = os.path.join(out_dir, "libaccr.so")
     r = subprocess.run([nvcc()] + NVCC_FLAGS + list(defines) + ["-c", src, "-o", obj], capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed for a batch variant:\n%s%s" % (r.stdout, r.stderr))
+        raise RuntimeError("nvcc failed for a variant of %s:\n%s%s" % (source, r.stdout, r.stderr))
     objs = [o for o in (os.path.join(BUILD, os.path.basename(x)[:-3] + ".o") for x in _sources())
-            if not o.endswith(os.sep + "batch.o")]
+            if os.path.basename(o) != source[:-3] + ".o"]
     r = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", lib, obj] + objs + ["-lpthread", "-ldl", "-lrt"],
                        capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("link failed for a batch variant:\n%s%s" % (r.stdout, r.stderr))
+        raise RuntimeError("link failed for a variant of %s:\n%s%s" % (source, r.stdout, r.stderr))
     return lib
+
+
+def build_batch_variant(defines, out_dir):
+    return build_variant("batch.cu", defines, out_dir)
 
 
 if __name__ == "__main__":

@@ -23,7 +23,12 @@
 namespace accr {
 
 constexpr int RB = 512;          // threads per CTA
-constexpr int RU = 4;            // 16-byte vectors per thread per iteration
+// 16-byte vectors per thread per iteration: picked by the autotuner
+// ("vectors" in tuning.json), passed in by the build.
+#ifndef ACCR_REDUCE_RU
+#define ACCR_REDUCE_RU 4
+#endif
+constexpr int RU = ACCR_REDUCE_RU;
 constexpr int kMaxGrid = 4096;   // bound on CTAs (and partials per clause)
 
 struct ReduceArgs {

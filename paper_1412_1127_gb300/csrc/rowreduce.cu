@@ -35,7 +35,12 @@ namespace accr {
 
 
 constexpr int WB = 256;  // threads per CTA (8 warps = 8 rows in flight)
-constexpr int RU2 = 8;   // 16-byte vectors per lane per iteration
+// 16-byte vectors per lane per iteration: picked by the autotuner ("vectors"
+// in tuning.json), passed in by the build.
+#ifndef ACCR_ROW_RU
+#define ACCR_ROW_RU 8
+#endif
+constexpr int RU2 = ACCR_ROW_RU;
 constexpr int64_t SPLIT_ROW_BYTES = 256 * 1024;
 constexpr int64_t SPLIT_CHUNK_BYTES = 32 * 1024;
 

@@ -80,3 +80,17 @@ def test_vector_widths_reach_the_build(tmp_path):
     got = json.loads(table.read_text())
     assert got["vectors"]["tile_vectors"] == 4 and got["vectors"]["timings_ms"]["8,16,3"]["2^20"] == 1.38
     assert got["small_bytes"] == 65536
+
+
+def test_each_kernels_widths_reach_its_own_source(tmp_path):
+    """The single-region and row kernels' widths go to their own sources only."""
+    from paper_1412_1127_gb300 import build
+    table = tmp_path / "tuning.json"
+    table.write_text(json.dumps({"small_bytes": 65536, "tile_bytes": 2097152}))
+    autotune.save_widths("reduce", (8,), {(2,): {"i32": 0.3}, (8,): {"i32": 0.2}}, path=str(table))
+    autotune.save_widths("rows", (16,), {(16,): {"65536x4096": 0.15}}, path=str(table))
+    assert build.tuned_defines(str(table), "reduce.cu") == ["-DACCR_REDUCE_RU=8"]
+    assert build.tuned_defines(str(table), "rowreduce.cu") == ["-DACCR_ROW_RU=16"]
+    assert build.tuned_defines(str(table), "batch.cu") == []
+    assert build.tuned_defines(str(table), "server.cu") == []
+    assert json.loads(table.read_text())["vectors"]["reduce_timings_ms"]["2"]["i32"] == 0.3
