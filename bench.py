@@ -80,7 +80,9 @@ def measured_peaks():
 def source_hash(files):
     """Hash of the device code of the given sources: a .cu file counts from its
     first __global__ kernel to the "// ---- host side" marker (host-only edits
-    do not change the kernel), a header counts whole."""
+    do not change the kernel), together with the autotuned widths the build
+    compiles into it; a header counts whole."""
+    from paper_1412_1127_gb300 import build
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
@@ -89,6 +91,7 @@ def source_hash(files):
             a = txt.find(b"__global__")
             b = txt.find(b"// ---- host side")
             txt = txt[a:b] if a >= 0 and b > a else txt
+            txt += " ".join(build.tuned_defines(source=os.path.basename(f))).encode()
         h.update(txt)
     return h.hexdigest()[:16]
 

@@ -37,6 +37,15 @@ def test_traffic_record_is_dropped_when_the_kernel_changes(tmp_path, monkeypatch
     src.write_text(text[:i] + " /* changed */" + text[i:])
     assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is None
     assert bench.ncu_traffic("no_such_kernel", "scalar_2^28", REDUCE_SOURCES) is None
+    # ... and so does another autotuned width compiled into the same source
+    src.write_text(text)
+    assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is not None
+    from paper_1412_1127_gb300 import build
+    real = build.tuned_defines
+    monkeypatch.setattr(build, "tuned_defines",
+                        lambda table=None, source="batch.cu": real(table, source) + (["-DACCR_REDUCE_RU=2"]
+                                                                                  if source == "reduce.cu" else []))
+    assert bench.ncu_traffic("reduce_kernel", "scalar_2^28", REDUCE_SOURCES) is None
 
 
 def test_whole_job_rate_counts_every_rank():
