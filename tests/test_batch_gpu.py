@@ -255,3 +255,55 @@ def test_plain_form_matches_batched():
     for k, (_, cls, _) in enumerate(regions):
         for c, want in zip(cls, res[k]):
             assert c.out.cpu().numpy()[0] == want
+
+
+def test_segmented_many_segments_three_clauses():
+    """More than 4,096 segments (the plan is built in chunks on the planner
+    threads) with three clauses (two descriptors per segment): every segment
+    against the oracle."""
+    g = np.random.default_rng(31)
+    L = np.exp(g.uniform(0, np.log(200000), size=7000)).astype(np.int64)
+    L[::97] = 0
+    off = inputs.offsets_from_lengths(L)
+    v = inputs.uniform_i64(int(off[-1]), -(1 << 40), 1 << 40, salt=12)
+    vt = torch.from_numpy(v).cuda()
+    outs = [guarded((len(L),), torch.int64, 3) for _ in range(3)]
+    ops = ["add", "bxor", "max"]
+    api.accr_segmented_reduce(vt, off, [api.clause(op, o.t) for op, o in zip(ops, outs)])
+    for op, o in zip(ops, outs):
+        assert np.array_equal(o.check(op).cpu().numpy(), oracle.segmented_reduce(v, off, op, "i64")), op
+
+
+def test_concurrent_one_shot_batches_from_two_threads():
+    """Two host threads plan and launch large one-shot batches at the same time
+    on their own streams (plans of 4,096 regions or more share the planner
+    threads): every result against the oracle, three rounds each."""
+    import threading
+    g = np.random.default_rng(41)
+    L = np.exp(g.uniform(0, np.log(50000), size=5000)).astype(np.int64)
+    off = inputs.offsets_from_lengths(L)
+    v = inputs.uniform_i64(int(off[-1]), -(1 << 40), 1 << 40, salt=13)
+    vt = torch.from_numpy(v).cuda()
+    want = {"add": oracle.segmented_reduce(v, off, "add", "i64"), "bxor": oracle.segmented_reduce(v, off, "bxor", "i64")}
+    errors = []
+
+    def worker(op, seed):
+        try:
+            s = torch.cuda.Stream()
+            out = torch.empty(len(L), dtype=torch.int64, device="cuda")
+            regions = [(vt[off[k]:off[k + 1]], [api.clause(op, out[k:k + 1])], 0) for k in range(len(L))]
+            for _ in range(3):
+                out.fill_(-1)
+                torch.cuda.synchronize()
+                api.accr_batch_reduce(regions, flags=api.ACCR_SYNC, stream=s)
+                if not np.array_equal(out.cpu().numpy(), want[op]):
+                    errors.append(op)
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    ts = [threading.Thread(target=worker, args=(op, i)) for i, op in enumerate(["add", "bxor"])]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
