@@ -479,6 +479,18 @@ ACCR_API uint64_t accr_launch_count(void);
 /* ABI version of this header (major * 100 + minor). */
 ACCR_API int32_t accr_version(void);
 
+/* Bounds checks of debug builds (a substitute for a memory checker; no
+ * counterpart in the paper).  A library built with ACCR_DEBUG
+ * (libaccr_debug.so) checks the index of every global store of the row,
+ * batched-region, k-nearest and tensor-core kernels against its bound; a
+ * failed check does not trap: it counts a violation, records the first
+ * failing site and skips the access.  This call (after the work has finished:
+ * synchronise first) returns the number of violations since the last clear,
+ * the first failing site (0 if none; the codes are listed in the library's
+ * debug.cuh) and whether the library checks at all (*checked = 0 in release
+ * builds, where both counts are 0); clear != 0 resets the counts. */
+ACCR_API int accr_debug_report(uint64_t *violations, uint32_t *first_site, int32_t *checked, int32_t clear);
+
 #define ACCR_VERSION 100
 
 #ifdef __cplusplus

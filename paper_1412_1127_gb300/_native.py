@@ -7,7 +7,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libaccr.so")
+# The library: the in-tree release build, or another build of it named by
+# ACCR_LIBRARY (the debug build, libaccr_debug.so, for bounds-checked runs).
+LIB_PATH = os.environ.get("ACCR_LIBRARY") or os.path.join(_HERE, "libaccr.so")
 
 # status codes of include/accr.h
 ACCR_OK = 0
@@ -78,6 +80,8 @@ SIGNATURES = {
     "accr_selftest_wait_timeout": (ctypes.c_int, [_u32, _vp]),
     "accr_probe_fma": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
     "accr_probe_fma_packed": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
+    "accr_debug_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "accr_last_error": (ctypes.c_char_p, []),
     "accr_launch_count": (_u64, []),
     "accr_version": (_i32, []),

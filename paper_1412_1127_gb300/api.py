@@ -381,3 +381,11 @@ def accr_launch_count():
 
 def accr_version():
     return int(lib().accr_version())
+
+
+def accr_debug_report(clear=True):
+    """(violations, first failing site, checked) of a debug build's bounds
+    checks; checked is False for release builds (see include/accr.h)."""
+    v, site, chk = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_int32()
+    check(lib().accr_debug_report(ctypes.byref(v), ctypes.byref(site), ctypes.byref(chk), int(bool(clear))))
+    return int(v.value), int(site.value), bool(chk.value)

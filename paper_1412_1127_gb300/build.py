@@ -17,6 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaccr.so")
+DEBUG_BUILD = os.path.join(PKG, "_build_debug")
+DEBUG_LIB = os.path.join(PKG, "libaccr_debug.so")  # bounds-checked build (-DACCR_DEBUG)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
@@ -67,11 +69,15 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, jobs=None, defines=None, build_dir=None, lib=None):
+def build(force=False, verbose=False, jobs=None, defines=None, build_dir=None, lib=None, debug=False):
     """Compile and link libaccr.so if any source, header or the tuning table
     changed.  `defines` ({source name: [flags]}), `build_dir` and `lib`
-    override the tuned definitions and the output paths."""
+    override the tuned definitions and the output paths; debug=True builds
+    the bounds-checked library libaccr_debug.so (-DACCR_DEBUG) instead."""
+    if debug:
+        build_dir, lib = build_dir or DEBUG_BUILD, lib or DEBUG_LIB
     build_dir, lib = build_dir or BUILD, lib or LIB
+    extra = ["-DACCR_DEBUG"] if debug else []
     os.makedirs(build_dir, exist_ok=True)
     srcs, hdrs = _sources(), _headers()
     table = os.path.join(PKG, "tuning.json")
@@ -90,7 +96,7 @@ def build(force=False, verbose=False, jobs=None, defines=None, build_dir=None, l
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc()] + NVCC_FLAGS + defs_for(s) + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc()] + NVCC_FLAGS + extra + defs_for(s) + ["-c", s, "-o", o + ".tmp"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

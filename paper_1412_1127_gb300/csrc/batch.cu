@@ -33,6 +33,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
+#include "debug.cuh"
 #include "fold.cuh"
 
 namespace accr {
@@ -77,6 +78,8 @@ struct BatchArgs {
     const int2 *tiles;           // [T] (region, tile index in region), in queue order
     const int32_t *small;        // [S] warp regions, in queue order
     int64_t T, S;
+    int64_t R;                   // descriptors (bound of the region indices)
+    int64_t slots;               // partial slots (tiles of all tiled descriptors)
     int64_t tile_bytes;
     Partial *partials;           // [sum of tiles][RD_CLAUSES], slot tile0 + k
     unsigned *counters;          // [R] tiles done per region; zero on entry and exit
@@ -114,6 +117,7 @@ __device__ __noinline__ void tile_fold(const BatchArgs &p, const RegionDev *d, i
     const int64_t len = (n - lo) < TE ? (n - lo) : TE;
     const int64_t ntiles = (n + TE - 1) / TE;
     const T *in = (const T *)d->in + lo;
+    if (!ACCR_DCHECK(k >= 0 && k < ntiles, DS_BATCH_TILE)) return;  // the same for the whole CTA
 
     int w[NC];
     uint64_t id[NC];
@@ -174,7 +178,7 @@ __device__ __noinline__ void tile_fold(const BatchArgs &p, const RegionDev *d, i
             q.a = A[c].a;
             q.c = A[c].c;
             q.pad = 0;
-            p.partials[t * RD_CLAUSES + c] = q;
+            if (ACCR_DCHECK(t >= 0 && t < p.slots, DS_BATCH_SLOT)) p.partials[t * RD_CLAUSES + c] = q;
         }
         __threadfence();
         const unsigned old = atomicAdd(&p.counters[r], 1u);
@@ -185,6 +189,7 @@ __device__ __noinline__ void tile_fold(const BatchArgs &p, const RegionDev *d, i
     __syncthreads();
     if (!last) return;
     __threadfence();
+    const bool slots_ok = ACCR_DCHECK(tile0 >= 0 && tile0 + ntiles <= p.slots, DS_BATCH_SLOT);
     int fw[NC];
     uint64_t fid[NC];
 #pragma unroll
@@ -193,7 +198,7 @@ __device__ __noinline__ void tile_fold(const BatchArgs &p, const RegionDev *d, i
         fid[c] = final_ident(d->cl[c]);
         A[c].a = fid[c];
         A[c].c = 0.f;
-        for (int64_t j = threadIdx.x; j < ntiles; j += BB) {
+        for (int64_t j = threadIdx.x; slots_ok && j < ntiles; j += BB) {
             Partial q = ld_partial_cg(&p.partials[(tile0 + j) * RD_CLAUSES + c]);
             Acc Q;
             Q.a = q.a;
@@ -292,9 +297,11 @@ __device__ __forceinline__ void batch_body(const BatchArgs &p, const RegionDev *
     while (q < p.T) {
         if (threadIdx.x == 0) s_q = (long long)atomicAdd(&p.queue[0], 1u);
         const int2 tk = tiles[q];
-        const RegionDev *d = regions + tk.x;
-        const int type = d->in_type, nc = d->nc;
-        ACCR_DISPATCH_TYPE_NC(type, nc, tile_fold, p, d, tk.x, (int64_t)tk.y, sh, &s_last);
+        if (ACCR_DCHECK(tk.x >= 0 && tk.x < p.R, DS_BATCH_REGION)) {  // the same for the whole CTA
+            const RegionDev *d = regions + tk.x;
+            const int type = d->in_type, nc = d->nc;
+            ACCR_DISPATCH_TYPE_NC(type, nc, tile_fold, p, d, tk.x, (int64_t)tk.y, sh, &s_last);
+        }
         __syncthreads();
         q = s_q;
         __syncthreads();
@@ -307,9 +314,12 @@ __device__ __forceinline__ void batch_body(const BatchArgs &p, const RegionDev *
     while (s < p.S) {
         long long nx = 0;
         if (lane == 0) nx = (long long)atomicAdd(&p.queue[1], 1u);
-        const RegionDev *d = regions + small[s];
-        const int type = d->in_type, nc = d->nc;
-        ACCR_DISPATCH_TYPE_NC(type, nc, warp_fold, d, lane);
+        const int32_t ri = small[s];
+        if (ACCR_DCHECK(ri >= 0 && ri < p.R, DS_BATCH_REGION)) {
+            const RegionDev *d = regions + ri;
+            const int type = d->in_type, nc = d->nc;
+            ACCR_DISPATCH_TYPE_NC(type, nc, warp_fold, d, lane);
+        }
         s = __shfl_sync(0xffffffffu, nx, 0);
     }
     // the last CTA to finish returns the queues to zero for the next launch
@@ -787,6 +797,8 @@ static BatchArgs args_for(const HostPlan &P, char *dev, unsigned *counters) {
     a.small = (const int32_t *)(dev + P.off_small);
     a.T = (int64_t)P.tiles.size();
     a.S = (int64_t)P.small.size();
+    a.R = (int64_t)P.regions.size();
+    a.slots = P.ntiles;
     a.tile_bytes = P.tile_bytes;
     a.partials = (Partial *)(dev + P.off_partials);
     a.queue = counters;         // 4 words: the queues

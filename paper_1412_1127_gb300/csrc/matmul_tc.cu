@@ -36,6 +36,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "debug.cuh"
 
 namespace accr {
 
@@ -261,8 +262,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const bool store = !*abort;
             const int m0 = (tile / tiles_n) * TBM, n0 = (tile % tiles_n) * TBN;
+            // a tile with no element inside c means the host's tile count is wrong
+            const bool store = !*abort && ACCR_DCHECK(m0 < M && n0 < N, DS_GEMM_STORE);
             const int row = m0 + q * 32 + lane;
 #pragma unroll 1
             for (int ch = 0; ch < TBN / 32; ++ch) {

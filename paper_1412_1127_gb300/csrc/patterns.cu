@@ -33,6 +33,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "debug.cuh"
 #include "fold.cuh"
 
 namespace accr {
@@ -483,7 +484,11 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
             p.i = MI[j];
             p.d = MD[j];
             p.pad = 0;
-            partials[(int64_t)blockIdx.x * KT + j] = p;
+            // the slots end where the sample's minima begin
+            if (ACCR_DCHECK((int64_t)blockIdx.x * KT + j < (int64_t)((const char *)minima - (const char *)partials) /
+                                                              (int64_t)sizeof(PairSlot),
+                            DS_NEAREST_SLOT))
+                partials[(int64_t)blockIdx.x * KT + j] = p;
         }
         __threadfence();
         am_last = atomicAdd(counter, 1u) == (unsigned)G - 1u;
@@ -494,7 +499,8 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
     final_lists<KT, NT>(partials, (int64_t)G * KT, LD, LI);
     cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
     if (threadIdx.x == 0) {
-        for (int j = 0; j < k; ++j) {
+        const int kk = ACCR_DCHECK(k >= 1 && k <= KT, DS_NEAREST_OUT) ? k : 0;  // the list holds KT entries
+        for (int j = 0; j < kk; ++j) {
             const bool real = MI[j] != INT64_MAX;
             idx_out[j] = real ? MI[j] : -1;
             d_out[j] = real ? MD[j] : INFINITY;

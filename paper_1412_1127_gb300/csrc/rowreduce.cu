@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "debug.cuh"
 #include "fold.cuh"
 
 namespace accr {
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
             if (lane == 0) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
-                    store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, to_final(w[c], A[c])));
+                    if (ACCR_DCHECK(r < p.rows, DS_ROW_VAR))
+                        store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, to_final(w[c], A[c])));
             }
         }
         return;
@@ -157,7 +159,9 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
     const int64_t k1 = (k0 + p.per_warp) < total ? (k0 + p.per_warp) : total;
     for (int64_t k = k0; k < k1; ++k) {
         const int64_t r = k / p.cpr, j = k - r * p.cpr, lo = j * p.chunk;
-        fold_stretch<T, NC>(p, w, r, lo, (cols - lo) < p.chunk ? (cols - lo) : p.chunk, lane, A);
+        const int64_t len = (cols - lo) < p.chunk ? (cols - lo) : p.chunk;
+        if (!ACCR_DCHECK(r < p.rows && lo + len <= cols, DS_ROW_CHUNK)) continue;
+        fold_stretch<T, NC>(p, w, r, lo, len, lane, A);
         if (lane == 0) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -165,7 +169,8 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
                 q.a = A[c].a;
                 q.c = A[c].c;
                 q.pad = 0;
-                p.partials[(r * NC + c) * p.cpr + j] = q;
+                if (ACCR_DCHECK((r * NC + c) * p.cpr + j < p.rows * NC * p.cpr, DS_ROW_PARTIAL))
+                    p.partials[(r * NC + c) * p.cpr + j] = q;
             }
         }
     }
@@ -180,7 +185,8 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
         const int64_t a = (r * p.cpr > c0 ? r * p.cpr : c0), b = ((r + 1) * p.cpr < c1 ? (r + 1) * p.cpr : c1);
         if (threadIdx.x == 0) {
             __threadfence();
-            s_last = (atomicAdd(&p.counters[r], (unsigned)(b - a)) + (unsigned)(b - a)) == (unsigned)p.cpr;
+            s_last = ACCR_DCHECK(r < p.rows, DS_ROW_COUNTER) &&
+                     (atomicAdd(&p.counters[r], (unsigned)(b - a)) + (unsigned)(b - a)) == (unsigned)p.cpr;
         }
         __syncthreads();
         if (s_last) {
@@ -213,7 +219,8 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
             cta_merge<NC, WB>(fw, fid, E64, A, sh);
             if (threadIdx.x == 0) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, A[c]));
+                for (int c = 0; c < NC; ++c)
+                    if (ACCR_DCHECK(r < p.rows, DS_ROW_VAR)) store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, A[c]));
                 p.counters[r] = 0u;
             }
         }

@@ -11,10 +11,12 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
+#include "debug.cuh"
 
 namespace accr {
 
@@ -229,6 +231,36 @@ extern "C" ACCR_API uint64_t accr_launch_count(void) {
 }
 
 extern "C" ACCR_API int32_t accr_version(void) { return ACCR_VERSION; }
+
+// ---- debug builds: readers of the translation units' status words -----------------
+namespace accr {
+static std::vector<DebugReader> &debug_readers() {
+    static std::vector<DebugReader> *v = new std::vector<DebugReader>();  // filled during static init
+    return *v;
+}
+void debug_register(DebugReader reader) { debug_readers().push_back(reader); }
+}  // namespace accr
+
+extern "C" ACCR_API int accr_debug_report(uint64_t *violations, uint32_t *first_site, int32_t *checked,
+                                          int32_t clear) {
+    accr::clear_error();
+    if (!violations || !first_site || !checked) return accr::set_error(ACCR_EINVAL, "accr_debug_report: NULL argument");
+    *violations = 0;
+    *first_site = 0;
+#ifdef ACCR_DEBUG
+    *checked = 1;
+#else
+    *checked = 0;
+#endif
+    for (accr::DebugReader r : accr::debug_readers()) {
+        unsigned long long n = 0, site = 0;
+        if (r(&n, &site, clear != 0) != ACCR_OK)
+            return accr::set_error(ACCR_ECUDA, "accr_debug_report: reading a status word failed");
+        *violations += n;
+        if (!*first_site && site) *first_site = (uint32_t)site;
+    }
+    return ACCR_OK;
+}
 
 extern "C" ACCR_API int accr_fault_inject(int32_t kind, int64_t count) {
     accr::clear_error();

@@ -128,3 +128,13 @@ def test_log_level_reports_errors_on_stderr(L):
     assert quiet.stdout.strip() == loud.stdout.strip() == str(_native.ACCR_EINVAL)
     assert "accr:" not in quiet.stderr
     assert "accr: error %d: accr_reduce: n = -1 < 0" % _native.ACCR_EINVAL in loud.stderr
+
+
+def test_release_build_reports_no_bounds_checks(L):
+    """accr_debug_report on the release library: no checks compiled in, nothing
+    counted, and no CUDA call made (so it runs without a GPU)."""
+    if os.path.basename(_native.LIB_PATH) != "libaccr.so":
+        pytest.skip("another library was selected with ACCR_LIBRARY")
+    from paper_1412_1127_gb300 import api
+    assert api.accr_debug_report(clear=True) == (0, 0, False)
+    assert api.accr_debug_report(clear=False) == (0, 0, False)
