@@ -289,10 +289,11 @@ ACCR_API int accr_batch_tiling(int64_t small_bytes, int64_t tile_bytes,
  * (qx, qy).  d_i = (x_i - qx)^2 + (y_i - qy)^2 in float, every operation
  * rounded (no fused multiply-add); the k smallest by (d, i), ties by index,
  * in increasing order -- a reduction whose operator keeps a sorted list.
- * For n >= 2^22 the (cooperative) launch first takes the k-th smallest
- * distance of a 65,536-point sample as a bound (k real points lie within
- * it), so the scan tests only points within the bound one by one; results do
- * not depend on it.
+ * One launch.  Each warp starts from a distance bound that k of its own
+ * first points reach; for n >= 2^22 the launch also takes the k-th smallest
+ * of per-CTA minima over a sample spread across the array and publishes it
+ * while the scan runs (no CTA waits for it).  Only points within the
+ * current bound are tested one by one; results do not depend on the bounds.
  *
  *   pts       DEVICE, n points as float pairs (x0, y0, x1, y1, ...), 8-byte aligned
  *   idx_out   DEVICE int64[k]; d2_out DEVICE float[k] (-1 / +inf past n)

@@ -4,10 +4,11 @@
 //  * Nearest Neighbor: distances to a query point and the k smallest -- a
 //    reduction whose operator keeps a sorted list of k (distance, index)
 //    pairs.  Each warp keeps one list in shared memory and tests a whole round
-//    of its points against the list's k-th distance at once; a distance bound
-//    taken from a sample of the points at the start of the (cooperative)
-//    launch keeps the lists' slow path rare.  The CTA ranks its warps' entries, and the
-//    last CTA to finish merges the CTA lists.
+//    of its points against the list's k-th distance at once; distance bounds
+//    (a warp's first round, then one taken from a sample of the whole array
+//    and published while the scan runs) keep the lists' slow path rare.  The
+//    CTA ranks its warps' entries, and the last CTA to finish ranks the few
+//    CTA entries that can still be among the k smallest.
 //
 //  * SRAD: a reduction region whose result feeds a data-parallel region.  The
 //    paper's OpenACC code merges the block partials on the CPU and launches
@@ -177,10 +178,12 @@ __device__ __forceinline__ float sqdist(float x, float y, float qx, float qy) {
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));  // no fused multiply-add
 }
 
-// One list per warp in shared memory; every lane keeps the warp's current
-// k-th entry (the threshold) in registers.  A lane's candidate that beats the
-// threshold is found by a ballot; such candidates (rare once the list has
-// filled, or from the start under the sampled bound) go through the
+// One list per warp in shared memory, kept sorted in the (distance, index)
+// order; its first k entries are the warp's k smallest so far, and every
+// lane keeps the k-th (the threshold) in registers.  Entries past the k-th
+// never rise above it, so they never matter.  A lane's candidate that beats
+// the threshold is found by a ballot; such candidates (rare once the list
+// holds real points, or from the start under a bound) go through the
 // out-of-line slow path one at a time, lane 0 inserting into the shared list.
 struct Thr {
     float d;
@@ -188,15 +191,15 @@ struct Thr {
 };
 
 template <int KT>
-__device__ __noinline__ Thr warp_insert_slow(float *LD, int64_t *LI, float d, int64_t i, unsigned mask) {
+__device__ __noinline__ Thr warp_insert_slow(float *LD, int64_t *LI, int k, float d, int64_t i, unsigned mask) {
     const int lane = threadIdx.x & 31;
     while (mask) {
         const int src = __ffs(mask) - 1;
         mask &= mask - 1;
         const float cd = __shfl_sync(0xffffffffu, d, src);
         const int64_t ci = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
-        if (lane == 0 && pless(cd, ci, LD[KT - 1], LI[KT - 1])) {
-            int j = KT - 1;
+        if (lane == 0 && pless(cd, ci, LD[k - 1], LI[k - 1])) {
+            int j = k - 1;
             while (j > 0 && pless(cd, ci, LD[j - 1], LI[j - 1])) {
                 LD[j] = LD[j - 1];
                 LI[j] = LI[j - 1];
@@ -208,8 +211,8 @@ __device__ __noinline__ Thr warp_insert_slow(float *LD, int64_t *LI, float d, in
         __syncwarp();
     }
     Thr t;
-    t.d = LD[KT - 1];
-    t.i = LI[KT - 1];
+    t.d = LD[k - 1];
+    t.i = LI[k - 1];
     __syncwarp();
     return t;
 }
@@ -218,9 +221,46 @@ __device__ __noinline__ Thr warp_insert_slow(float *LD, int64_t *LI, float d, in
 // superset of the winners (ties included); the slow path applies the exact
 // (distance, index) order.
 template <int KT>
-__device__ __forceinline__ void warp_offer(float *LD, int64_t *LI, Thr &thr, float d, int64_t i) {
+__device__ __forceinline__ void warp_offer(float *LD, int64_t *LI, int k, Thr &thr, float d, int64_t i) {
     const unsigned mask = __ballot_sync(0xffffffffu, d <= thr.d);
-    if (mask) thr = warp_insert_slow<KT>(LD, LI, d, i, mask);
+    if (mask) thr = warp_insert_slow<KT>(LD, LI, k, d, i, mask);
+}
+
+// A distance bound B that at least k distinct points reach may stand in for
+// k placeholders (B, no index): every entry of the list at or past (B, no
+// index) becomes one (the prefix below it stays), so the list keeps the k
+// smallest of what it held and the placeholders.  Returns the new threshold.
+template <int KT>
+__device__ __noinline__ Thr warp_apply_bound(float *LD, int64_t *LI, int k, float B) {
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < KT; ++j)
+            if (!pless(LD[j], LI[j], B, INT64_MAX)) {
+                LD[j] = B;
+                LI[j] = INT64_MAX;
+            }
+    }
+    __syncwarp();
+    Thr t;
+    t.d = LD[k - 1];
+    t.i = LI[k - 1];
+    __syncwarp();
+    return t;
+}
+
+// The k-th smallest of one value per lane (k <= 32; every lane gets it).
+__device__ __forceinline__ float warp_kth_smallest(float v, int k) {
+    const int lane = threadIdx.x & 31;
+    float t = INFINITY;
+    for (int r = 0; r < k; ++r) {
+        float w = v;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
+        t = w;
+        const unsigned who = __ballot_sync(0xffffffffu, v == w);
+        if (lane == __ffs(who) - 1) v = INFINITY;  // exactly one lane gives up its value
+    }
+    return t;
 }
 
 // The CTA's KT smallest of its warps' lists (shared memory), written to
@@ -286,19 +326,17 @@ __device__ __noinline__ void final_lists(const PairSlot *partials, int64_t nc, f
         }
 }
 
-// The bound: the first NK_BOUND_CTAS CTAs of the scan launch each take a
-// share of a sample (NK_CHUNKS chunks of NK_CHUNK consecutive points, spread
-// evenly over the array: chunk c starts at point c * stride) and every warp
-// records the smallest distance of its share; those minima belong to
-// distinct points, so the k-th smallest of them is a distance that at least
-// k points reach.  The last sampling CTA selects it and publishes it; every
-// CTA waits for it (bounded: if the wait runs out, the scan proceeds without
-// a bound, which changes its speed, not its result).
-constexpr int NK_CHUNK = 512, NK_CHUNKS = 128, NK_BOUND_CTAS = 64;
-constexpr int NK_BOUND_WARPS = NK_BOUND_CTAS * (NK_THREADS / 32);  // 512 minima
-constexpr int64_t NK_BOUND_MIN_N = 1 << 22;  // smaller inputs skip the bound
-constexpr int NK_BOUND_PER_THREAD = NK_CHUNK * (NK_CHUNKS / NK_BOUND_CTAS) / NK_THREADS;
-constexpr uint32_t kBoundSpin = 1u << 20;    // polls of the published bound (~0.1 s)
+// The sampled bound.  Every CTA of the scan launch takes NK_SAMPLE
+// consecutive points at blockIdx.x * sample_stride (so the sample spreads
+// over the whole array) and records its smallest distance; those minima
+// belong to distinct points, so the k-th smallest of them is a distance that
+// at least k points reach.  The last CTA to record its minimum selects it and
+// publishes it as one word (its bits + 1; zero means not yet).  Nobody waits
+// for it: each warp polls the word once per round and applies the bound when
+// it appears; until then its first round's own k-th smallest lane minimum
+// serves as a bound.
+constexpr int NK_SAMPLE = NK_THREADS;        // points sampled per CTA (one per thread)
+constexpr int64_t NK_BOUND_MIN_N = 1 << 22;  // smaller inputs skip the sampled bound
 
 template <int KT>
 __device__ __forceinline__ void flist_insert(float (&D)[KT], float d) {
@@ -308,37 +346,20 @@ __device__ __forceinline__ void flist_insert(float (&D)[KT], float d) {
     D[0] = d < D[0] ? d : D[0];
 }
 
-// Warp minima of this CTA's share of the sample (one per warp, to minima[]).
-__device__ __forceinline__ void sample_minima(const float2 *__restrict__ pts, int64_t stride, float qx, float qy,
-                                              float *minima) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 v[NK_BOUND_PER_THREAD];
-#pragma unroll
-    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) {  // every load first
-        const int t = e * NK_THREADS + threadIdx.x;   // point t of this CTA's chunks
-        const int c = blockIdx.x * (NK_CHUNKS / NK_BOUND_CTAS) + t / NK_CHUNK;
-        v[e] = __ldg(pts + (int64_t)c * stride + (t % NK_CHUNK));
-    }
-    float m = INFINITY;  // fminf passes over NaN distances
-#pragma unroll
-    for (int e = 0; e < NK_BOUND_PER_THREAD; ++e) m = fminf(m, sqdist(v[e].x, v[e].y, qx, qy));
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) minima[blockIdx.x * (NK_THREADS / 32) + warp] = m;
-}
-
-// The k-th smallest of the NK_BOUND_WARPS minima (one warp; every lane gets it).
+// The k-th smallest of cnt values (one warp; every lane gets it; k <= KT).
 template <int KT>
-__device__ __forceinline__ float kth_of_minima(const float *minima, int k) {
+__device__ __forceinline__ float kth_of_values(const float *v, int cnt, int k) {
     const int lane = threadIdx.x & 31;
-    constexpr int PER_LANE = NK_BOUND_WARPS / 32;
-    float D[KT], mv[PER_LANE];
+    float D[KT];
 #pragma unroll
     for (int j = 0; j < KT; ++j) D[j] = INFINITY;
+    for (int j0 = lane; j0 < cnt; j0 += 32 * 8) {
+        float mv[8];
 #pragma unroll
-    for (int j = 0; j < PER_LANE; ++j) mv[j] = __ldcg(minima + j * 32 + lane);  // all loads in flight
+        for (int u = 0; u < 8; ++u) mv[u] = (j0 + 32 * u < cnt) ? __ldcg(v + j0 + 32 * u) : INFINITY;  // in flight together
 #pragma unroll
-    for (int j = 0; j < PER_LANE; ++j) flist_insert<KT>(D, mv[j]);
+        for (int u = 0; u < 8; ++u) flist_insert<KT>(D, mv[u]);
+    }
     // k rounds of a warp minimum, each taking the head of exactly one lane
     float t = INFINITY;
     for (int r = 0; r < k; ++r) {
@@ -356,12 +377,83 @@ __device__ __forceinline__ float kth_of_minima(const float *minima, int k) {
     return t;
 }
 
-// With sample_stride > 0 (a cooperative launch of at least NK_BOUND_CTAS
-// CTAs) the kernel first takes the sampled bound T: every list starts as KT
-// placeholders (T, no index), so only points with d <= T are ever tested in
-// the slow path; since k real points lie within T, the placeholders never
-// reach the output.  bstate[0..2]: sampling CTAs arrived, bound published,
-// bound bits; zero on entry and exit.
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Last CTA: the k smallest of the G CTA lists (each sorted) by k rounds of a
+// tournament over the lists' heads.  Thread t holds the heads of lists t and
+// t + NT and the entry after each (loaded ahead, so the winner of a round
+// seldom waits for its next entry); a round takes the CTA-wide smallest
+// (distance, index, list) and its list advances.  Returns false (nothing
+// written) for more than 2 NT lists; the caller then merges every slot.
+template <int KT, int NT>
+__device__ __noinline__ bool final_tournament(const PairSlot *partials, int G, int k, float *MD, int64_t *MI) {
+    __shared__ float wd[2][NT / 32];
+    __shared__ int64_t wi[2][NT / 32];
+    __shared__ int wo[2][NT / 32];
+    if (G > 2 * NT) return false;  // uniform across the CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NONE = 0x7fffffff;  // no list
+    auto slot = [&](int L, int j, float &d, int64_t &i) {
+        if (L < G && j < k) {
+            const uint4 r = __ldcg(reinterpret_cast<const uint4 *>(partials + (int64_t)L * KT + j));
+            d = __uint_as_float(r.z);
+            i = (int64_t)(((uint64_t)r.y << 32) | r.x);
+        } else {
+            d = INFINITY;
+            i = INT64_MAX;
+        }
+    };
+    const int L0 = threadIdx.x, L1 = threadIdx.x + NT;
+    float h0, n0, h1, n1;
+    int64_t g0, m0, g1, m1;
+    slot(L0, 0, h0, g0);
+    slot(L1, 0, h1, g1);
+    slot(L0, 1, n0, m0);
+    slot(L1, 1, n1, m1);
+    int p0 = 0, p1 = 0;
+    for (int r = 0; r < k; ++r) {
+        const bool second = pless(h1, g1, h0, g0);  // ties: the lower list
+        float d = second ? h1 : h0;
+        int64_t i = second ? g1 : g0;
+        int o = (second ? L1 : L0) < G ? (second ? L1 : L0) : NONE;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, d, s);
+            const int64_t oi = (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)i, s);
+            const int oo = __shfl_xor_sync(0xffffffffu, o, s);
+            if (pless(od, oi, d, i) || (od == d && oi == i && oo < o)) d = od, i = oi, o = oo;
+        }
+        if (lane == 0) wd[r & 1][warp] = d, wi[r & 1][warp] = i, wo[r & 1][warp] = o;
+        __syncthreads();
+        d = wd[r & 1][0], i = wi[r & 1][0], o = wo[r & 1][0];
+#pragma unroll
+        for (int w = 1; w < NT / 32; ++w) {
+            const float od = wd[r & 1][w];
+            const int64_t oi = wi[r & 1][w];
+            const int oo = wo[r & 1][w];
+            if (pless(od, oi, d, i) || (od == d && oi == i && oo < o)) d = od, i = oi, o = oo;
+        }
+        if (threadIdx.x == 0) MD[r] = d, MI[r] = i;
+        if (o == L0) {  // the winner's list advances; the entry after the new head is loaded ahead
+            h0 = n0, g0 = m0, ++p0;
+            slot(L0, p0 + 1, n0, m0);
+        } else if (o == L1) {
+            h1 = n1, g1 = m1, ++p1;
+            slot(L1, p1 + 1, n1, m1);
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// With sample_stride > 0 every CTA samples, the last one publishes the
+// sampled bound in bstate[1], and warps pick it up as described above.
+// bstate[0] counts the CTAs that recorded their sample minimum; the last CTA
+// of the launch returns both words to zero.
 template <int KT, int NT>
 __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict__ pts, int64_t n, float qx, float qy,
                                                      int k, int64_t *idx_out, float *d_out, PairSlot *partials,
@@ -371,93 +463,118 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
     __shared__ int64_t wli[NT / 32][KT];
     __shared__ float MD[KT];
     __shared__ int64_t MI[KT];
+    __shared__ float s_min[NT / 32];
     __shared__ int am_last;
-    __shared__ float s_T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *LD = wld[warp];
     int64_t *LI = wli[warp];
-    float T = INFINITY;
-    if (sample_stride > 0) {
-        if (blockIdx.x < NK_BOUND_CTAS) {
-            sample_minima((const float2 *)pts, sample_stride, qx, qy, minima);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                am_last = atomicAdd(&bstate[0], 1u) == (unsigned)NK_BOUND_CTAS - 1u;
-            }
-            __syncthreads();
-            if (am_last && warp == 0) {
-                __threadfence();
-                const float t = kth_of_minima<KT>(minima, k);
-                if (lane == 0) {
-                    bstate[2] = __float_as_uint(t);
-                    __threadfence();
-                    st_release(&bstate[1], 1u);
-                }
-            }
-        }
-        if (threadIdx.x == 0) {  // every CTA waits for the bound, a bounded number of polls
-            uint32_t i = 0;
-            unsigned f = ld_acquire(&bstate[1]);
-            while (f == 0u && ++i <= kBoundSpin) {
-                __nanosleep(64);
-                f = ld_acquire(&bstate[1]);
-            }
-            s_T = f ? __uint_as_float(*(volatile unsigned *)&bstate[2]) : INFINITY;
-        }
-        __syncthreads();
-        T = s_T;
-    }
     if (lane < KT) {
-        LD[lane] = T;
+        LD[lane] = INFINITY;
         LI[lane] = INT64_MAX;
     }
     __syncwarp();
     Thr thr;
-    thr.d = T;
+    thr.d = INFINITY;
     thr.i = INT64_MAX;
     // points are float2; the vector part starts at a 16-byte boundary
     const int64_t head = (((uintptr_t)pts & 15) != 0 && n > 0) ? 1 : 0;
     const float4 *v4 = (const float4 *)(pts + 2 * head);
     const int64_t npairs = (n - head) / 2;
     const int64_t nth = (int64_t)gridDim.x * NT;
+    // Full rounds: NU 16-byte loads (2 points each) per lane, every one in
+    // range, so no per-point bounds test; the round's smallest distance is
+    // compared once with the warp's k-th, and only a round in which some lane
+    // beats it tests its points.  The trip count is uniform across each warp
+    // so that the votes see 32 lanes.
+    constexpr int NU = 16;
+    const int64_t vstep = nth * NU;
+    int64_t vb = (int64_t)blockIdx.x * (NT * NU) + warp * 32;
+    float4 q[NU];
+    bool full = vb + (NU - 1) * NT + 31 < npairs;  // uniform across the warp
+    if (full) {  // the first round's loads go out before the sample
+        const float4 *p = v4 + vb + lane;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) q[u] = ld_pts(p + u * NT);
+    }
+    bool poll = false;
+    if (sample_stride > 0) {
+        const float2 sp = __ldg((const float2 *)pts + (int64_t)blockIdx.x * sample_stride + threadIdx.x);
+        float m = sqdist(sp.x, sp.y, qx, qy);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_min[warp] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float cm = s_min[0];
+#pragma unroll
+            for (int w = 1; w < NT / 32; ++w) cm = fminf(cm, s_min[w]);  // fminf passes over NaN
+            minima[blockIdx.x] = cm;
+            __threadfence();
+            am_last = atomicAdd(&bstate[0], 1u) == gridDim.x - 1u;
+        }
+        __syncthreads();
+        if (am_last && warp == 0) {
+            __threadfence();
+            const float t = kth_of_values<KT>(minima, (int)gridDim.x, k);
+            if (lane == 0) st_release(&bstate[1], __float_as_uint(t) + 1u);  // t in [0, inf]: never wraps to 0
+        }
+        poll = true;
+    }
     if (blockIdx.x == 0 && warp == 0) {  // the unaligned first point and the odd last point
         const int64_t last = head + 2 * npairs;
         float d = INFINITY;
         int64_t i = INT64_MAX;
         if (lane == 0 && head) d = sqdist(pts[0], pts[1], qx, qy), i = 0;
         if (lane == 1 && last < n) d = sqdist(pts[2 * last], pts[2 * last + 1], qx, qy), i = last;
-        warp_offer<KT>(LD, LI, thr, d, i);
+        warp_offer<KT>(LD, LI, k, thr, d, i);
     }
-    // Full rounds: NU 16-byte loads (2 points each) per lane, every one in
-    // range, so no per-point bounds test; the round's smallest distance is
-    // compared once with the warp's k-th, and only a round in which some lane
-    // beats it tests its points one by one.  The trip count is uniform across
-    // each warp so that the votes see 32 lanes.
-    constexpr int NU = 16;
-    const int64_t vstep = nth * NU;
-    int64_t vb = (int64_t)blockIdx.x * (NT * NU) + warp * 32;
-    for (; vb + (NU - 1) * NT + 31 < npairs; vb += vstep) {
-        const float4 *p = v4 + vb + lane;
-        float4 q[NU];
-#pragma unroll
-        for (int u = 0; u < NU; ++u) q[u] = ld_pts(p + u * NT);
+    while (full) {
+        const unsigned pb = (poll && lane == 0) ? ld_relaxed(&bstate[1]) : 0u;  // the bound, if published
         float dm = INFINITY;
 #pragma unroll
         for (int u = 0; u < NU; ++u)
             dm = fminf(dm, fminf(sqdist(q[u].x, q[u].y, qx, qy), sqdist(q[u].z, q[u].w, qx, qy)));
+        if (poll) {
+            const unsigned b = __shfl_sync(0xffffffffu, pb, 0);
+            if (b != 0u) {
+                const float B = __uint_as_float(b - 1u);
+                if (B < thr.d) thr = warp_apply_bound<KT>(LD, LI, k, B);
+                poll = false;
+            }
+        }
+        if (thr.d == INFINITY && k <= 32) {  // no bound yet: the k-th smallest lane minimum of this round
+            const float B = warp_kth_smallest(dm, k);   // k distinct points reach it
+            if (B < thr.d) thr = warp_apply_bound<KT>(LD, LI, k, B);
+        }
         if (__any_sync(0xffffffffu, dm <= thr.d)) {
-            // recompute the distances (the same arithmetic) rather than keep
-            // them in registers: the registers go to the loads in flight
-            const int64_t ibase = head + 2 * (vb + lane);  // this lane's first point this round
+            // the points of this lane that beat the threshold now (it only
+            // falls, so later winners are among them), then one pass over
+            // the positions some lane has, in order
+            unsigned bits = 0u;
 #pragma unroll
             for (int j = 0; j < 2 * NU; ++j) {
                 const float4 &v = q[j >> 1];
                 const float dj = (j & 1) ? sqdist(v.z, v.w, qx, qy) : sqdist(v.x, v.y, qx, qy);
-                // the threshold may drop between the points: test each again
-                const unsigned mask = __ballot_sync(0xffffffffu, dj <= thr.d);
-                if (mask) thr = warp_insert_slow<KT>(LD, LI, dj, ibase + 2 * (j >> 1) * NT + (j & 1), mask);
+                bits |= (dj <= thr.d ? 1u : 0u) << j;
             }
+            const unsigned any = __reduce_or_sync(0xffffffffu, bits);
+            const int64_t ibase = head + 2 * (vb + lane);  // this lane's first point this round
+#pragma unroll
+            for (int j = 0; j < 2 * NU; ++j) {
+                if (any & (1u << j)) {  // uniform across the warp
+                    const float4 &v = q[j >> 1];
+                    const float dj = (j & 1) ? sqdist(v.z, v.w, qx, qy) : sqdist(v.x, v.y, qx, qy);
+                    const unsigned mask = __ballot_sync(0xffffffffu, ((bits >> j) & 1u) && dj <= thr.d);
+                    if (mask) thr = warp_insert_slow<KT>(LD, LI, k, dj, ibase + 2 * (j >> 1) * NT + (j & 1), mask);
+                }
+            }
+        }
+        vb += vstep;
+        full = vb + (NU - 1) * NT + 31 < npairs;
+        if (full) {
+            const float4 *p = v4 + vb + lane;
+#pragma unroll
+            for (int u = 0; u < NU; ++u) q[u] = ld_pts(p + u * NT);
         }
     }
     if (vb < npairs) {  // the last, partial round: points past the end never compete
@@ -466,13 +583,13 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
         for (int u = 0; u < NU; ++u) {
             const int64_t vv = vb + lane + u * NT;
             const bool ok = vv < npairs;
-            const float4 q = ok ? ld_pts(v4 + vv) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float d0 = ok ? sqdist(q.x, q.y, qx, qy) : INFINITY;
-            const float d1 = ok ? sqdist(q.z, q.w, qx, qy) : INFINITY;
+            const float4 v = ok ? ld_pts(v4 + vv) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float d0 = ok ? sqdist(v.x, v.y, qx, qy) : INFINITY;
+            const float d1 = ok ? sqdist(v.z, v.w, qx, qy) : INFINITY;
             unsigned mask = __ballot_sync(0xffffffffu, ok && d0 <= thr.d);
-            if (mask) thr = warp_insert_slow<KT>(LD, LI, d0, ibase + 2 * u * NT, mask);
+            if (mask) thr = warp_insert_slow<KT>(LD, LI, k, d0, ibase + 2 * u * NT, mask);
             mask = __ballot_sync(0xffffffffu, ok && d1 <= thr.d);
-            if (mask) thr = warp_insert_slow<KT>(LD, LI, d1, ibase + 2 * u * NT + 1, mask);
+            if (mask) thr = warp_insert_slow<KT>(LD, LI, k, d1, ibase + 2 * u * NT + 1, mask);
         }
     }
     cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
@@ -496,8 +613,10 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    final_lists<KT, NT>(partials, (int64_t)G * KT, LD, LI);
-    cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
+    if (!final_tournament<KT, NT>(partials, G, k, MD, MI)) {
+        final_lists<KT, NT>(partials, (int64_t)G * KT, LD, LI);
+        cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
+    }
     if (threadIdx.x == 0) {
         const int kk = ACCR_DCHECK(k >= 1 && k <= KT, DS_NEAREST_OUT) ? k : 0;  // the list holds KT entries
         for (int j = 0; j < kk; ++j) {
@@ -506,7 +625,7 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
             d_out[j] = real ? MD[j] : INFINITY;
         }
         *counter = 0u;
-        if (sample_stride > 0) {  // every CTA read the bound before its scan
+        if (sample_stride > 0) {  // every CTA has recorded its minimum and stopped polling
             bstate[0] = 0u;
             bstate[1] = 0u;
         }
@@ -526,30 +645,22 @@ static int nearest_launch(const float *pts, int64_t n, float qx, float qy, int k
     const DeviceInfo &di = device_info();
     const int64_t want = (n / 2 + NT * 16 - 1) / (NT * 16);  // one round of 16 vectors per thread
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
-    // the bound needs its sampling CTAs resident with the others: a cooperative launch
-    const bool use_bound = n >= NK_BOUND_MIN_N && grid >= NK_BOUND_CTAS;
-    // scratch: [partials: grid * KT slots][the sample's warp minima]
+    // a sample of NK_SAMPLE points per CTA, spread over the array
+    const bool use_bound = n >= NK_BOUND_MIN_N && grid >= 32 && n / grid >= NK_SAMPLE;
+    // scratch: [partials: grid * KT slots][the CTAs' sample minima]
     const size_t part_bytes = sizeof(PairSlot) * (size_t)grid * KT;
     const size_t minima_off = (part_bytes + 255) & ~(size_t)255;
-    Scratch *scr = scratch_for((accr_stream_t)s, minima_off + sizeof(float) * NK_BOUND_WARPS);
+    Scratch *scr = scratch_for((accr_stream_t)s, minima_off + sizeof(float) * (size_t)grid);
     if (!scr) return ACCR_ENOMEM;
     PairSlot *partials = (PairSlot *)scr->buf;
     unsigned *counter = scr->counters + 1;
-    unsigned *bstate = scr->counters + 5;  // words 5-7
+    unsigned *bstate = scr->counters + 5;  // words 5-6
     float *minima = (float *)((char *)scr->buf + minima_off);
-    int64_t stride = use_bound ? n / NK_CHUNKS : 0;
+    const int64_t stride = use_bound ? n / grid : 0;
     int rc = launch_guard("nearest_kernel");
     if (rc != ACCR_OK) return rc;
-    if (use_bound) {
-        void *args[] = {(void *)&pts, (void *)&n, (void *)&qx, (void *)&qy, (void *)&k, (void *)&idx, (void *)&d,
-                        (void *)&partials, (void *)&counter, (void *)&stride, (void *)&minima, (void *)&bstate};
-        rc = cuda_check(cudaLaunchCooperativeKernel((const void *)nearest_kernel<KT, NT>, grid, NT, args, 0, s),
-                        "accr_nearest_k: cooperative launch");
-        if (rc != ACCR_OK) return rc;
-    } else {
-        nearest_kernel<KT, NT><<<grid, NT, 0, s>>>(pts, n, qx, qy, k, idx, d, partials, counter, stride, minima,
-                                                    bstate);
-    }
+    // no CTA waits for another: a plain launch
+    nearest_kernel<KT, NT><<<grid, NT, 0, s>>>(pts, n, qx, qy, k, idx, d, partials, counter, stride, minima, bstate);
     return launched("nearest_kernel");
 }
 

@@ -158,3 +158,22 @@ def test_nearest_k_full_size():
     wi, wd = oracle.nearest_k(pts, 41.5, 58.25, 5)
     assert np.array_equal(gi.check("idx").cpu().numpy(), wi)
     assert np.array_equal(gd.check("d2").cpu().numpy(), wd)
+
+
+@pytest.mark.parametrize("k", [5, 8])
+def test_nearest_k_fewer_real_points_than_k(k):
+    """All but three points have NaN coordinates (a NaN distance never enters
+    a list, in the oracle as here): the three real points come first and the
+    rest of the k are empty (-1, inf), with every CTA list but three holding
+    placeholders only."""
+    n = (1 << 22) + 5
+    pts = np.full((n, 2), np.nan, dtype=np.float32)
+    for i, v in [(17, 1.0), (n // 2, 3.0), (n - 1, 2.0)]:
+        pts[i] = (v, v)
+    pt = torch.from_numpy(pts).cuda()
+    gi, gd = guarded((k,), torch.int64, -7), guarded((k,), torch.float32, -7)
+    api.accr_nearest_k(pt, 0.0, 0.0, k, gi.t, gd.t, flags=api.ACCR_SYNC)
+    wi, wd = oracle.nearest_k(pts, 0.0, 0.0, k)
+    assert list(wi[:3]) == [17, n - 1, n // 2] and all(wi[3:] == -1)
+    assert np.array_equal(gi.check("idx").cpu().numpy(), wi)
+    assert np.array_equal(gd.check("d2").cpu().numpy(), wd)
