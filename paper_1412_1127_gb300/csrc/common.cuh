@@ -67,6 +67,12 @@ Scratch *scratch_for(accr_stream_t stream, size_t bytes);
 // Pinned host staging of at least `bytes` for `stream` (for D2H of partials).
 void *host_staging_for(accr_stream_t stream, size_t bytes);
 
+// At least `n` device words for `stream` on the current device that are zero
+// whenever no kernel is using them: cleared on the stream when created or
+// grown, and every kernel that takes them returns each word it touched to
+// zero before it exits.  Returns nullptr (and sets the error) on failure.
+unsigned *zeroed_words_for(accr_stream_t stream, size_t n);
+
 // ---- types ----------------------------------------------------------------
 inline int type_bytes(int t) { return (t == ACCR_I32 || t == ACCR_F32) ? 4 : 8; }
 inline bool type_is_int(int t) { return t == ACCR_I32 || t == ACCR_I64; }

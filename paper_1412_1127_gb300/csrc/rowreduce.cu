@@ -13,15 +13,19 @@
 //     lane 0 writes the row's variable; no cross-warp merge at all.
 //   * longer rows: the stretch is one of the row's SPLIT_CHUNK_BYTES chunks
 //     (a few long rows then spread over every SM instead of a few warps).
-//     Each resident warp takes a contiguous run of chunks (the same number
-//     for every warp, to within the last run) and lane 0 stores each chunk's
-//     partial in the chunk's own slot; when its eight warps are done the CTA
-//     counts its chunks into each row it touched, and the CTA whose count
-//     completes a row merges the row's partials in chunk order (thread t
-//     takes chunks t, t + 256, ..., four loads in flight, then the CTA's
+//     The launch has one 1024-thread CTA per SM (256-thread CTAs, as many as
+//     fit, where the fold needs more registers), and CTA b
+//     takes the contiguous run [total b / G, total (b + 1) / G) of the
+//     rows x cpr chunks, so every SM streams the same number of chunks to
+//     within one; its 32 warps take the run's chunks in turn, so the warps
+//     left with a last chunk are many and keep the SM's loads in flight.
+//     Lane 0 stores each chunk's partial in the chunk's own slot; the CTA
+//     then counts its chunks into each row it touched, and the CTA whose
+//     count completes a row merges the row's partials in chunk order (thread
+//     t takes chunks t, t + 1024 (or 256), ..., loads in flight, then the CTA's
 //     shuffle and shared-memory tree) and writes the variable.  The partial
-//     slots and the merge order depend on the row length only, not on which
-//     warp folded which chunk.
+//     slots and the merge order depend on the row length and the clauses
+//     only, not on which warp folded which chunk.
 #include <string.h>
 
 #include <atomic>
@@ -35,7 +39,14 @@
 namespace accr {
 
 
-constexpr int WB = 256;  // threads per CTA (8 warps = 8 rows in flight)
+constexpr int WB = 256;  // threads per CTA of the warp-per-row form (8 rows in flight)
+// Threads per CTA of the split form: 1024 (one CTA per SM) where the fold
+// fits 64 registers (4-byte elements, one or two clauses), else 256 (as many
+// CTAs per SM as the registers allow).
+template <typename T, int NC, bool SPLIT>
+constexpr int row_threads() {
+    return !SPLIT ? WB : (sizeof(T) == 4 && NC <= 2) ? 1024 : 256;
+}
 // 16-byte vectors per lane per iteration: picked by the autotuner ("vectors"
 // in tuning.json), passed in by the build.
 #ifndef ACCR_ROW_RU
@@ -52,9 +63,8 @@ struct RowArgs {
     ClauseDev cl[ACCR_MAX_CLAUSES];
     int64_t chunk;        // split form: elements per chunk
     int64_t cpr;          // split form: chunks per row
-    int64_t per_warp;     // split form: chunks of each warp's contiguous run
     Partial *partials;    // split form: [rows][nc][cpr]
-    unsigned *counters;   // split form: [rows], zero on entry, zero again on exit
+    unsigned *counters;   // split form: [rows], zero on entry, zero again on exit (zeroed_words_for)
 };
 
 __device__ __forceinline__ Partial ld_row_partial(const Partial *p) {
@@ -127,10 +137,11 @@ __device__ __forceinline__ void fold_stretch(const RowArgs &p, const int (&w)[NC
 // fold's operator switch then disappears from the row loop); -1 reads them
 // from the arguments.  SPLIT selects the chunked form for long rows.
 template <typename T, int NC, int W0 = -1, int W1 = -1, bool SPLIT = false>
-__global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ RowArgs p) {
+__global__ void __launch_bounds__(row_threads<T, NC, SPLIT>()) rowreduce_kernel(const __grid_constant__ RowArgs p) {
     constexpr bool E64 = sizeof(T) == 8;
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * (WB / 32) + (threadIdx.x >> 5);
+    constexpr int NTH = row_threads<T, NC, SPLIT>(), NW = NTH / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * NW + warp;
     const int64_t cols = p.cols;
     int w[NC];
 #pragma unroll
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
     Acc A[NC];
 
     if (!SPLIT) {
-        const int64_t warps = (int64_t)gridDim.x * (WB / 32);
+        const int64_t warps = (int64_t)gridDim.x * NW;
         for (int64_t r = gw; r < p.rows; r += warps) {
             fold_stretch<T, NC>(p, w, r, 0, cols, lane, A);
             if (lane == 0) {
@@ -150,14 +161,11 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
         }
         return;
     }
-    // chunks k0 .. k1-1 (a contiguous run) of the rows x cpr chunks; the
-    // CTA's eight runs are contiguous too
-    __shared__ Acc sh[NC][WB / 32];
-    __shared__ int s_last;
+    // this CTA's run of the rows x cpr chunks, its warps taking them in turn
+    __shared__ Acc sh[NC][NW];
     const int64_t total = p.rows * p.cpr;
-    const int64_t k0 = gw * p.per_warp;
-    const int64_t k1 = (k0 + p.per_warp) < total ? (k0 + p.per_warp) : total;
-    for (int64_t k = k0; k < k1; ++k) {
+    const int64_t c0 = total * (int64_t)blockIdx.x / gridDim.x, c1 = total * ((int64_t)blockIdx.x + 1) / gridDim.x;
+    for (int64_t k = c0 + warp; k < c1; k += NW) {
         const int64_t r = k / p.cpr, j = k - r * p.cpr, lo = j * p.chunk;
         const int64_t len = (cols - lo) < p.chunk ? (cols - lo) : p.chunk;
         if (!ACCR_DCHECK(r < p.rows && lo + len <= cols, DS_ROW_CHUNK)) continue;
@@ -174,23 +182,34 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
             }
         }
     }
-    // the CTA counts its chunks into each row it touched; the CTA whose count
-    // completes a row merges the row's partials in chunk order (thread t takes
-    // chunks t, t + WB, ..., four loads in flight, then the CTA tree)
-    const int64_t c0 = (int64_t)blockIdx.x * (WB / 32) * p.per_warp;
-    const int64_t c1 = (c0 + (WB / 32) * p.per_warp) < total ? (c0 + (WB / 32) * p.per_warp) : total;
+    // the CTA counts its chunks into each row it touched, thread t into row
+    // r0 + t (an acquire-release add: it releases the CTA's partials, which
+    // the barrier before it ordered, and the add that completes a row
+    // acquires every other CTA's); the CTA then merges each row it completed
+    // in chunk order (thread t takes chunks t, t + NTH, ..., loads in flight,
+    // then the CTA tree)
+    __shared__ int64_t s_rows[NTH];
+    __shared__ int s_nd;
     __syncthreads();
-    if (c0 >= total) return;  // uniform across the CTA
-    for (int64_t r = c0 / p.cpr; r <= (c1 - 1) / p.cpr; ++r) {
-        const int64_t a = (r * p.cpr > c0 ? r * p.cpr : c0), b = ((r + 1) * p.cpr < c1 ? (r + 1) * p.cpr : c1);
-        if (threadIdx.x == 0) {
-            __threadfence();
-            s_last = ACCR_DCHECK(r < p.rows, DS_ROW_COUNTER) &&
-                     (atomicAdd(&p.counters[r], (unsigned)(b - a)) + (unsigned)(b - a)) == (unsigned)p.cpr;
+    if (c0 >= c1) return;  // uniform across the CTA
+    const int64_t r0 = c0 / p.cpr, r1 = (c1 - 1) / p.cpr;
+    for (int64_t rb = r0; rb <= r1; rb += NTH) {
+        if (threadIdx.x == 0) s_nd = 0;
+        __syncthreads();
+        const int64_t r = rb + threadIdx.x;
+        if (r <= r1 && ACCR_DCHECK(r < p.rows, DS_ROW_COUNTER)) {
+            const int64_t a = (r * p.cpr > c0 ? r * p.cpr : c0), b = ((r + 1) * p.cpr < c1 ? (r + 1) * p.cpr : c1);
+            unsigned old;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                         : "=r"(old)
+                         : "l"(&p.counters[r]), "r"((unsigned)(b - a))
+                         : "memory");
+            if (old + (unsigned)(b - a) == (unsigned)p.cpr) s_rows[atomicAdd(&s_nd, 1)] = r;
         }
         __syncthreads();
-        if (s_last) {
-            __threadfence();
+        const int nd = s_nd;
+        for (int iq = 0; iq < nd; ++iq) {
+            const int64_t rr = s_rows[iq];
             int fw[NC];
             uint64_t fid[NC];
 #pragma unroll
@@ -199,32 +218,38 @@ __global__ void __launch_bounds__(WB) rowreduce_kernel(const __grid_constant__ R
                 fid[c] = final_ident(p.cl[c]);
                 A[c].a = fid[c];
                 A[c].c = 0.f;
-                const Partial *pp = &p.partials[(r * NC + c) * p.cpr];
-                for (int64_t b0 = threadIdx.x; b0 < p.cpr; b0 += WB * 4) {
-                    Partial q[4];
+            }
+            constexpr int U = NC == 1 ? 4 : NC == 2 ? 2 : 1;  // loads in flight per clause and thread
+            for (int64_t b0 = threadIdx.x; b0 < p.cpr; b0 += (int64_t)NTH * U) {
+                Partial q[NC][U];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (b0 + u * WB < p.cpr) q[u] = ld_row_partial(pp + b0 + u * WB);
+                for (int c = 0; c < NC; ++c)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (b0 + u * WB < p.cpr) {
+                    for (int u = 0; u < U; ++u)
+                        if (b0 + u * NTH < p.cpr)
+                            q[c][u] = ld_row_partial(&p.partials[(rr * NC + c) * p.cpr] + b0 + u * NTH);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (b0 + u * NTH < p.cpr) {
                             Acc Q;
-                            Q.a = q[u].a;
-                            Q.c = q[u].c;
+                            Q.a = q[c][u].a;
+                            Q.c = q[c][u].c;
                             merge(fw[c], E64, A[c], to_final(w[c], Q));
                         }
                     }
-                }
             }
-            cta_merge<NC, WB>(fw, fid, E64, A, sh);
+            cta_merge<NC, NTH>(fw, fid, E64, A, sh);
             if (threadIdx.x == 0) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
-                    if (ACCR_DCHECK(r < p.rows, DS_ROW_VAR)) store_var(p.cl[c], r, finish(p.cl[c], E64, cols == 0, A[c]));
-                p.counters[r] = 0u;
+                    if (ACCR_DCHECK(rr < p.rows, DS_ROW_VAR))
+                        store_var(p.cl[c], rr, finish(p.cl[c], E64, cols == 0, A[c]));
+                p.counters[rr] = 0u;
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -236,7 +261,8 @@ static int max_row_grid() {
     int g = slot.load(std::memory_order_relaxed);
     if (!g) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowreduce_kernel<T, NC, W0, W1, SPLIT>, WB, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowreduce_kernel<T, NC, W0, W1, SPLIT>,
+                                                      row_threads<T, NC, SPLIT>(), 0);
         if (per_sm < 1) per_sm = 1;
         g = per_sm * d.sms;
         slot.store(g, std::memory_order_relaxed);
@@ -244,21 +270,14 @@ static int max_row_grid() {
     return g;
 }
 
-// Warps for `segs` stretches: rows (one warp per row, at most the resident
-// grid, the rest in later rounds), or chunks of long rows (the resident warps,
-// each taking a contiguous run of the same number of chunks, to within the
-// last run).  Returns the CTA count; `per_warp` gets the run length.
+// CTAs for `segs` stretches: rows (one warp per row, at most the resident
+// grid, the rest in later rounds), or chunks of long rows (the resident grid,
+// at most one CTA per chunk, each CTA taking a contiguous run).
 template <typename T, int NC, int W0, int W1, bool SPLIT>
-static int row_grid(int64_t segs, int64_t *per_warp) {
-    const int64_t maxw = (int64_t)max_row_grid<T, NC, W0, W1, SPLIT>() * (WB / 32);
-    int64_t wantw = segs < maxw ? segs : maxw;
-    if (wantw < 1) wantw = 1;
-    if (SPLIT) {
-        *per_warp = (segs + wantw - 1) / wantw;
-        wantw = (segs + *per_warp - 1) / *per_warp;
-    }
-    const int64_t g = (wantw + WB / 32 - 1) / (WB / 32);
-    return (int)(g < 1 ? 1 : g);
+static int row_grid(int64_t segs) {
+    const int64_t maxg = max_row_grid<T, NC, W0, W1, SPLIT>();
+    const int64_t g = SPLIT ? segs : (segs + WB / 32 - 1) / (WB / 32);
+    return (int)(g < 1 ? 1 : g < maxg ? g : maxg);
 }
 
 template <typename T, int NC, int W0 = -1, int W1 = -1>
@@ -266,10 +285,10 @@ static int row_launch_t(RowArgs &a, cudaStream_t s) {
     int rc = launch_guard("rowreduce_kernel");
     if (rc != ACCR_OK) return rc;
     if (a.cpr > 0) {
-        const int g = row_grid<T, NC, W0, W1, true>(a.rows * a.cpr, &a.per_warp);
-        rowreduce_kernel<T, NC, W0, W1, true><<<g, WB, 0, s>>>(a);
+        rowreduce_kernel<T, NC, W0, W1, true>
+            <<<row_grid<T, NC, W0, W1, true>(a.rows * a.cpr), row_threads<T, NC, true>(), 0, s>>>(a);
     } else {
-        rowreduce_kernel<T, NC, W0, W1, false><<<row_grid<T, NC, W0, W1, false>(a.rows, nullptr), WB, 0, s>>>(a);
+        rowreduce_kernel<T, NC, W0, W1, false><<<row_grid<T, NC, W0, W1, false>(a.rows), WB, 0, s>>>(a);
     }
     return launched("rowreduce_kernel");
 }
@@ -349,13 +368,11 @@ extern "C" ACCR_API int accr_rowreduce(const void *A, int64_t rows, int64_t cols
         a.chunk = SPLIT_CHUNK_BYTES / eb;
         a.cpr = (cols + a.chunk - 1) / a.chunk;
         const size_t pbytes = (size_t)rows * (size_t)nclauses * (size_t)a.cpr * sizeof(Partial);
-        const size_t cbytes = (size_t)rows * sizeof(unsigned);
-        Scratch *scr = scratch_for(stream, pbytes + 256 + cbytes);
+        Scratch *scr = scratch_for(stream, pbytes);
         if (!scr) return ACCR_ENOMEM;
         a.partials = (Partial *)scr->buf;
-        a.counters = (unsigned *)((char *)scr->buf + ((pbytes + 255) & ~(size_t)255));
-        rc = cuda_check(cudaMemsetAsync(a.counters, 0, cbytes, s), "accr_rowreduce: clear row counters");
-        if (rc != ACCR_OK) return rc;
+        a.counters = zeroed_words_for(stream, (size_t)rows);  // every row completes, so each returns to zero
+        if (!a.counters) return ACCR_ENOMEM;
     }
     a.A = A;
     a.rows = rows;

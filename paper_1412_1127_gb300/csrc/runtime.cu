@@ -121,6 +121,8 @@ struct ScratchEntry {
     Scratch s{};
     void *host = nullptr;
     size_t host_bytes = 0;
+    unsigned *zw = nullptr;  // zeroed_words_for
+    size_t zw_n = 0;
     std::atomic<uint64_t> gen{0};  // bumped whenever `s` is replaced
 };
 static std::mutex g_scr_mu;
@@ -220,6 +222,37 @@ void *host_staging_for(accr_stream_t stream, size_t bytes) {
     }
     e->host_bytes = want;
     return e->host;
+}
+
+unsigned *zeroed_words_for(accr_stream_t stream, size_t n) {
+    std::lock_guard<std::mutex> lk(g_scr_mu);
+    ScratchEntry *e = entry_for(stream);
+    if (e->zw && e->zw_n >= n) return e->zw;
+    if (fault_take(ACCR_FAULT_ALLOC)) {
+        set_error(ACCR_ENOMEM, "zeroed words: injected allocation failure");
+        return nullptr;
+    }
+    if (e->zw) {  // work queued on this stream may still use the old words
+        if (cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "zeroed words grow") != ACCR_OK) return nullptr;
+        cudaFree(e->zw);
+        e->zw = nullptr;
+        e->zw_n = 0;
+    }
+    size_t want = n < 4096 ? 4096 : n;
+    if (cudaMalloc((void **)&e->zw, want * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        e->zw = nullptr;
+        set_error(ACCR_ENOMEM, "zeroed words: cudaMalloc of %zu words failed", want);
+        return nullptr;
+    }
+    if (cuda_check(cudaMemsetAsync(e->zw, 0, want * sizeof(unsigned), (cudaStream_t)stream), "zeroed words clear") !=
+        ACCR_OK) {
+        cudaFree(e->zw);
+        e->zw = nullptr;
+        return nullptr;
+    }
+    e->zw_n = want;
+    return e->zw;
 }
 
 }  // namespace accr
