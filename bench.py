@@ -966,7 +966,7 @@ def measure_rows(dev, rows=65536, cols=4096, steps=10, warmup=3):
     nbytes = rows * cols * 4
     peaks, kind = measured_peaks()
     ok_max = bool(torch.equal(m, At.amax(dim=1)))
-    form = "split-row (32 KiB chunks, warp runs, CTA merge)" if cols * 4 >= (256 << 10) else "one warp per row"
+    form = "split-row (32 KiB chunks, an even run per CTA, CTA merge)" if cols * 4 >= (256 << 10) else "one warp per row"
     return {"workload": "row sum + row max (one pass), %d x %d float U(-1,1)" % (rows, cols), "form": form,
             "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
             "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]), 4),
