@@ -101,69 +101,6 @@ __device__ __forceinline__ bool pless(float da, int64_t ia, float db, int64_t ib
     return da < db || (da == db && ia < ib);
 }
 
-template <int KT>
-__device__ __forceinline__ void list_init(float (&D)[KT], int64_t (&I)[KT]) {
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-        D[j] = INFINITY;
-        I[j] = INT64_MAX;
-    }
-}
-
-// Inserts (d, i) into the ascending list if it belongs to the KT smallest.
-template <int KT>
-__device__ __forceinline__ void list_insert(float (&D)[KT], int64_t (&I)[KT], float d, int64_t i) {
-    if (!pless(d, i, D[KT - 1], I[KT - 1])) return;
-    bool placed = false;
-#pragma unroll
-    for (int j = KT - 1; j > 0; --j) {
-        if (!placed) {
-            if (pless(d, i, D[j - 1], I[j - 1])) {
-                D[j] = D[j - 1];
-                I[j] = I[j - 1];
-            } else {
-                D[j] = d;
-                I[j] = i;
-                placed = true;
-            }
-        }
-    }
-    if (!placed) {
-        D[0] = d;
-        I[0] = i;
-    }
-}
-
-// Merges the 32 lanes' lists into the warp's KT smallest (every lane gets R).
-template <int KT>
-__device__ __forceinline__ void warp_topk(float (&D)[KT], int64_t (&I)[KT], float (&RD)[KT], int64_t (&RI)[KT]) {
-#pragma unroll
-    for (int r = 0; r < KT; ++r) {
-        float bd = D[0];
-        int64_t bi = I[0];
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) {
-            const float od = __shfl_xor_sync(0xffffffffu, bd, m);
-            const int64_t oi = (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)bi, m);
-            if (pless(od, oi, bd, bi)) {
-                bd = od;
-                bi = oi;
-            }
-        }
-        RD[r] = bd;
-        RI[r] = bi;
-        if (D[0] == bd && I[0] == bi) {  // my head was taken: pop it
-#pragma unroll
-            for (int j = 0; j < KT - 1; ++j) {
-                D[j] = D[j + 1];
-                I[j] = I[j + 1];
-            }
-            D[KT - 1] = INFINITY;
-            I[KT - 1] = INT64_MAX;
-        }
-    }
-}
-
 // Streaming 16-byte load of two points (read once: no L1 allocation).
 __device__ __forceinline__ float4 ld_pts(const float4 *p) {
     float4 v;
@@ -291,41 +228,6 @@ __device__ __forceinline__ void cta_merge_warp_lists(const float (*wld)[KT], con
     __syncthreads();
 }
 
-// Last CTA: every thread folds a strided share of the nc partial slots into
-// a list in registers (placeholders skipped), and each warp writes the top KT
-// of its lanes' lists to its shared-memory list.  Out of line, so that its
-// registers do not weigh on the scan loop.
-template <int KT, int NT>
-__device__ __noinline__ void final_lists(const PairSlot *partials, int64_t nc, float *LD, int64_t *LI) {
-    const int lane = threadIdx.x & 31;
-    float D[KT];
-    int64_t I[KT];
-    list_init<KT>(D, I);
-    constexpr int B = KT <= 8 ? 8 : 2;  // slots in flight per thread (the lists of 16 need the registers)
-    for (int64_t c0 = threadIdx.x; c0 < nc; c0 += (int64_t)B * NT) {
-        uint4 raw[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-            const int64_t c = c0 + (int64_t)u * NT;
-            raw[u] = c < nc ? __ldcg(reinterpret_cast<const uint4 *>(partials + c)) : make_uint4(~0u, 0x7fffffffu, 0u, 0u);
-        }
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-            const int64_t i = (int64_t)(((uint64_t)raw[u].y << 32) | raw[u].x);
-            if (i != INT64_MAX) list_insert<KT>(D, I, __uint_as_float(raw[u].z), i);
-        }
-    }
-    float RD[KT];
-    int64_t RI[KT];
-    warp_topk<KT>(D, I, RD, RI);
-#pragma unroll
-    for (int j = 0; j < KT; ++j)
-        if (j == lane) {
-            LD[j] = RD[j];
-            LI[j] = RI[j];
-        }
-}
-
 // The sampled bound.  Every CTA of the scan launch takes NK_SAMPLE
 // consecutive points at blockIdx.x * sample_stride (so the sample spreads
 // over the whole array) and records its smallest distance; those minima
@@ -383,18 +285,17 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
     return v;
 }
 
-// Last CTA: the k smallest of the G CTA lists (each sorted) by k rounds of a
-// tournament over the lists' heads.  Thread t holds the heads of lists t and
-// t + NT and the entry after each (loaded ahead, so the winner of a round
-// seldom waits for its next entry); a round takes the CTA-wide smallest
-// (distance, index, list) and its list advances.  Returns false (nothing
-// written) for more than 2 NT lists; the caller then merges every slot.
+// Last CTA: the k smallest of the G <= 2 NT CTA lists (each sorted) by k
+// rounds of a tournament over the lists' heads.  Thread t holds the heads of
+// lists t and t + NT and the entry after each (loaded ahead, so the winner of
+// a round seldom waits for its next entry); a round takes the CTA-wide
+// smallest (distance, index, list) and its list advances.
+constexpr int NK_MAX_GRID = 2 * NK_THREADS;  // CTA lists the tournament takes
 template <int KT, int NT>
-__device__ __noinline__ bool final_tournament(const PairSlot *partials, int G, int k, float *MD, int64_t *MI) {
+__device__ __noinline__ void final_tournament(const PairSlot *partials, int G, int k, float *MD, int64_t *MI) {
     __shared__ float wd[2][NT / 32];
     __shared__ int64_t wi[2][NT / 32];
     __shared__ int wo[2][NT / 32];
-    if (G > 2 * NT) return false;  // uniform across the CTA
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NONE = 0x7fffffff;  // no list
     auto slot = [&](int L, int j, float &d, int64_t &i) {
@@ -447,7 +348,6 @@ __device__ __noinline__ bool final_tournament(const PairSlot *partials, int G, i
         }
     }
     __syncthreads();
-    return true;
 }
 
 // With sample_stride > 0 every CTA samples, the last one publishes the
@@ -613,10 +513,7 @@ __global__ void __launch_bounds__(NT, 2) nearest_kernel(const float *__restrict_
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    if (!final_tournament<KT, NT>(partials, G, k, MD, MI)) {
-        final_lists<KT, NT>(partials, (int64_t)G * KT, LD, LI);
-        cta_merge_warp_lists<KT, NT>(wld, wli, MD, MI);
-    }
+    final_tournament<KT, NT>(partials, G, k, MD, MI);
     if (threadIdx.x == 0) {
         const int kk = ACCR_DCHECK(k >= 1 && k <= KT, DS_NEAREST_OUT) ? k : 0;  // the list holds KT entries
         for (int j = 0; j < kk; ++j) {
@@ -644,7 +541,8 @@ static int nearest_launch(const float *pts, int64_t n, float qx, float qy, int k
     });
     const DeviceInfo &di = device_info();
     const int64_t want = (n / 2 + NT * 16 - 1) / (NT * 16);  // one round of 16 vectors per thread
-    const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * di.sms);
+    const int64_t resident = std::min<int64_t>((int64_t)per_sm * di.sms, NK_MAX_GRID);
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), resident);
     // a sample of NK_SAMPLE points per CTA, spread over the array
     const bool use_bound = n >= NK_BOUND_MIN_N && grid >= 32 && n / grid >= NK_SAMPLE;
     // scratch: [partials: grid * KT slots][the CTAs' sample minima]
