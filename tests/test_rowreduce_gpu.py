@@ -165,3 +165,36 @@ def test_long_integer_rows_split_path():
                                api.clause("min", outs[2].t)])
         for o, (op, init) in zip(outs, [("add", None), ("bxor", 9), ("min", None)]):
             assert np.array_equal(o.check(op).cpu().numpy(), oracle.rowreduce(A, op, "i64", init=init)), (op, pad)
+
+
+@pytest.mark.parametrize("rows,cols", [(5, (1 << 18) + 13), (300, (1 << 16) + 3)])
+@pytest.mark.parametrize("pad,off", [(0, 0), (3, 1)])
+def test_split_rows_cross_runs_and_padding(rows, cols, pad, off):
+    """4-byte rows past the split-row threshold (one 1024-thread CTA per SM):
+    rows whose chunks start off the 16-byte grid (ld not a multiple of the
+    vector, an offset base), and CTA runs that end mid-row or cover several
+    rows, so one CTA counts into many rows and rows complete in any CTA.
+    Integer results bit-exact: a sum into int64 with a max (the fixed-code
+    pair), a lone int32 sum, and a float sum within its tolerance."""
+    g = np.random.default_rng(rows + pad)
+    A = g.integers(-1000, 1000, size=(rows, cols), dtype=np.int32)
+    big = np.zeros((rows, cols + pad + off), dtype=np.int32)
+    big[:, off:off + cols] = A
+    t = torch.from_numpy(big).cuda()[:, off:off + cols]
+    s64, mx = guarded((rows,), torch.int64, 5), guarded((rows,), torch.int32, 5)
+    api.accr_rowreduce(t, [api.clause("add", s64.t), api.clause("max", mx.t)])
+    assert np.array_equal(s64.check("sum").cpu().numpy(), oracle.rowreduce(A, "add", "i64"))
+    assert np.array_equal(mx.check("max").cpu().numpy(), oracle.rowreduce(A, "max", "i32"))
+    s32 = guarded((rows,), torch.int32, 5)
+    api.accr_rowreduce(t, [api.clause("add", s32.t, init=7)])
+    assert np.array_equal(s32.check("sum32").cpu().numpy(), oracle.rowreduce(A, "add", "i32", init=7))
+    F = (A.astype(np.float32) / np.float32(1000.0)).astype(np.float32)
+    fbig = np.zeros((rows, cols + pad + off), dtype=np.float32)
+    fbig[:, off:off + cols] = F
+    ft = torch.from_numpy(fbig).cuda()[:, off:off + cols]
+    fs = guarded((rows,), torch.float32, 5)
+    api.accr_rowreduce(ft, [api.clause("add", fs.t)])
+    got = fs.check("fsum").cpu().numpy()
+    for r in range(0, rows, max(1, rows // 16)):
+        truth = oracle.truth_sum(F[r])
+        assert abs(float(got[r]) - truth) / max(abs(truth), 0.1 * math.sqrt(cols) * 0.577) <= TOL_F32, r
