@@ -123,7 +123,8 @@ struct ScratchEntry {
     size_t host_bytes = 0;
     unsigned *zw = nullptr;  // zeroed_words_for
     size_t zw_n = 0;
-    std::atomic<uint64_t> gen{0};  // bumped whenever `s` is replaced
+    std::atomic<uint64_t> gen{0};     // bumped whenever `s` is replaced
+    std::atomic<uint64_t> zw_gen{0};  // bumped whenever `zw` is replaced
 };
 static std::mutex g_scr_mu;
 static std::map<std::pair<int, uintptr_t>, ScratchEntry *> g_scr;
@@ -224,10 +225,35 @@ void *host_staging_for(accr_stream_t stream, size_t bytes) {
     return e->host;
 }
 
+// Per-thread memo of the last (device, stream) zeroed words, as for scratch.
+struct ZeroedMemo {
+    int dev = -1;
+    accr_stream_t stream = nullptr;
+    ScratchEntry *e = nullptr;
+    uint64_t gen = 0;
+    size_t n = 0;
+    unsigned *zw = nullptr;
+};
+static thread_local ZeroedMemo t_zw;
+
 unsigned *zeroed_words_for(accr_stream_t stream, size_t n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (t_zw.e && t_zw.dev == dev && t_zw.stream == stream && n <= t_zw.n &&
+        t_zw.e->zw_gen.load(std::memory_order_acquire) == t_zw.gen)
+        return t_zw.zw;
     std::lock_guard<std::mutex> lk(g_scr_mu);
     ScratchEntry *e = entry_for(stream);
-    if (e->zw && e->zw_n >= n) return e->zw;
+    auto remember = [&] {
+        t_zw.dev = dev;
+        t_zw.stream = stream;
+        t_zw.e = e;
+        t_zw.gen = e->zw_gen.load(std::memory_order_relaxed);
+        t_zw.n = e->zw_n;
+        t_zw.zw = e->zw;
+        return e->zw;
+    };
+    if (e->zw && e->zw_n >= n) return remember();
     if (fault_take(ACCR_FAULT_ALLOC)) {
         set_error(ACCR_ENOMEM, "zeroed words: injected allocation failure");
         return nullptr;
@@ -237,6 +263,7 @@ unsigned *zeroed_words_for(accr_stream_t stream, size_t n) {
         cudaFree(e->zw);
         e->zw = nullptr;
         e->zw_n = 0;
+        e->zw_gen.fetch_add(1, std::memory_order_release);
     }
     size_t want = n < 4096 ? 4096 : n;
     if (cudaMalloc((void **)&e->zw, want * sizeof(unsigned)) != cudaSuccess) {
@@ -252,7 +279,8 @@ unsigned *zeroed_words_for(accr_stream_t stream, size_t n) {
         return nullptr;
     }
     e->zw_n = want;
-    return e->zw;
+    e->zw_gen.fetch_add(1, std::memory_order_release);
+    return remember();
 }
 
 }  // namespace accr
